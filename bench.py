@@ -1,0 +1,387 @@
+"""Benchmark of the parallel multicanonical 2D Ising hot path on GB300.
+
+Workload (the headline configuration): periodic 32x32 Ising lattices, 16384 walkers,
+int8 interleaved lattices, random +/-1 start (seed 1), 10 recorded sweeps per iteration
+after 31 thermalization sweeps, uint64 histogram over the 1025 energies, FP64 weight
+recursion; iteration budget 2e4 * L^2 recorded walker-sweeps (125 iterations).
+
+Reported:
+  value        spin-flip attempts per second over K weight-iteration steps (one step =
+               table build + upload, thermalization, zeroed histogram, recorded sweeps,
+               histogram read, flatness test and Eq. (4) recursion), device-timed with
+               CUDA events, L2 flushed between steps;
+  time_to_flat wall time of muca_iterate_until_flat from ln W = 0 until min/mean >= 0.8;
+  e2e          the same steps through the Python binding with host weights in and the
+               host histogram out (copies inside the timed region), host wall clock;
+  roofline     the recorded-sweep kernel against the integer-issue ceiling;
+  cpu_baseline the C oracle on the host cores for one step of the same workload.
+
+python bench.py [--gpus N] [--steps K] [--warmup W] [--impl native|reference]
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+L_SIDE = 32
+WALKERS = 16384
+SEED = 1
+THERM_SWEEPS = 31
+SWEEPS_PER_ITER = 10
+MAX_ITERATIONS = 2 * 10**4 * L_SIDE * L_SIDE // (WALKERS * SWEEPS_PER_ITER)   # 125
+# Algorithmic integer operations per attempted flip (Philox4x32-10: 10 rounds of 2
+# mul-hi, 2 mul-lo and 2 three-input XORs plus 9 key bumps of 2 adds = 78 per 4 words,
+# 19.5 per attempt; the flip: own spin, 4 neighbour compares, count, table address and
+# load, compare, conditional flip, energy update, run-length histogram record, about
+# 15.5).  Fixed by the method, not measured from the code.
+OPS_PER_ATTEMPT = 35.0
+WORKLOAD = (f"muca2d_ising_L{L_SIDE}_W{WALKERS}_int8_therm{THERM_SWEEPS}_rec{SWEEPS_PER_ITER}")
+
+
+def config_dict():
+    return {"workload": WORKLOAD, "L": L_SIDE, "walkers": WALKERS, "layout": "int8 [site][walker]",
+            "therm_sweeps": THERM_SWEEPS, "sweeps_per_iter": SWEEPS_PER_ITER, "energy_bins": L_SIDE**2 + 1,
+            "stop_rule": "min/mean >= 0.8", "max_iterations": MAX_ITERATIONS,
+            "l2": "flushed between timed steps (256 MiB write)", "parallelism": "independent instance per GPU"}
+
+
+# ----------------------------------------------------------------------------------
+# distributed plumbing
+# ----------------------------------------------------------------------------------
+def dist_env():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+def init_dist(ws):
+    if ws <= 1:
+        return None
+    import torch.distributed as dist
+    os.environ.setdefault("MASTER_ADDR", "127.0.0.1")
+    dist.init_process_group("gloo")
+    return dist
+
+
+def max_over_ranks(dist, x: float) -> float:
+    if dist is None:
+        return x
+    import torch
+    t = torch.tensor([x], dtype=torch.float64)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def barrier(dist):
+    if dist is not None:
+        dist.barrier()
+
+
+# ----------------------------------------------------------------------------------
+# clocks during the timed region
+# ----------------------------------------------------------------------------------
+class ClockSampler:
+    FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, device_index: int):
+        self.dev = device_index
+        self.proc = None
+        self.lines = []
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.dev), f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                 "-lms", "100"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.thread = threading.Thread(target=self._read, daemon=True)
+            self.thread.start()
+        except (OSError, ValueError):
+            self.proc = None
+        return self
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def __exit__(self, *exc):
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+
+    def summary(self):
+        sm, mx, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [p.strip() for p in ln.split(",")]
+            if len(parts) < 8:
+                continue
+            try:
+                sm.append(float(parts[0]))
+                mx = float(parts[1])
+            except ValueError:
+                continue
+            for name, val in zip(names, parts[4:8]):
+                if val.lower().startswith("active"):
+                    reasons.add(name)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": mx, "reasons": [], "samples": 0}
+        sm.sort()
+        return {"sm_mhz": sm[len(sm) // 2], "sm_max_mhz": mx, "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def measured_peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return json.load(f)
+    except (OSError, ValueError):
+        return {}
+
+
+# ----------------------------------------------------------------------------------
+# CPU baseline: the oracle on the host cores
+# ----------------------------------------------------------------------------------
+def _oracle_shard(args):
+    L, seed, w0, nw, lnW, t0, n_therm, n_rec = args
+    import numpy as np
+    from oracle import oracle
+    s, e = oracle.init(L, seed, nw, walker0=w0)
+    T = oracle.build_table(L, np.asarray(lnW))
+    t = time.perf_counter()
+    oracle.run(L, seed, s, e, T, t0, n_therm, False, None, walker0=w0)
+    H = oracle.run(L, seed, s, e, T, t0 + n_therm, n_rec, True, None, walker0=w0)
+    return time.perf_counter() - t, H
+
+
+def cpu_baseline(lnW, walkers: int, cores: int | None = None):
+    """One step (thermalization + recorded sweeps) of `walkers` walkers by the oracle,
+    walkers split across a spawn pool of host processes; returns attempts/s."""
+    import multiprocessing as mp
+    from oracle import oracle
+    oracle.build()
+    N = L_SIDE * L_SIDE
+    cores = cores or os.cpu_count() or 1
+    shard = (walkers + cores - 1) // cores
+    jobs = []
+    for c in range(cores):
+        w0 = c * shard
+        nw = min(shard, walkers - w0)
+        if nw > 0:
+            jobs.append((L_SIDE, SEED, w0, nw, list(lnW), 0, THERM_SWEEPS * N, SWEEPS_PER_ITER * N))
+    ctx = mp.get_context("spawn")
+    t0 = time.perf_counter()
+    with ctx.Pool(len(jobs)) as pool:
+        res = pool.map(_oracle_shard, jobs)
+    wall = time.perf_counter() - t0
+    busy = max(r[0] for r in res)
+    attempts = walkers * (THERM_SWEEPS + SWEEPS_PER_ITER) * N
+    return attempts / busy, len(jobs), wall
+
+
+# ----------------------------------------------------------------------------------
+# native arm
+# ----------------------------------------------------------------------------------
+def run_native(args):
+    import numpy as np
+    import torch
+
+    ws, rank, local = dist_env()
+    dist = init_dist(ws)
+    torch.cuda.set_device(local)
+    dev = torch.cuda.current_device()
+    import __graft_entry__
+    if rank == 0 or ws == 1:
+        __graft_entry__.build()
+    barrier(dist)
+    __graft_entry__.build()
+    from paper_1707_00919_gb300 import muca as M
+
+    N = L_SIDE * L_SIDE
+    stream = torch.cuda.Stream()
+    seed = SEED + rank                              # independent simulation per GPU
+    m = M.Muca(L_SIDE, WALKERS, seed, layout=M.MUCA_LAYOUT_INT8, stream=stream)
+
+    # ---- time to flat histogram (from ln W = 0) ----
+    params = M.make_params(therm_sweeps=THERM_SWEEPS, sweeps_per_iter=SWEEPS_PER_ITER,
+                           max_iterations=MAX_ITERATIONS)
+    barrier(dist)
+    t0 = time.perf_counter()
+    st = m.iterate_until_flat(params)
+    torch.cuda.synchronize()
+    ttf = time.perf_counter() - t0
+    ttf = max_over_ranks(dist, ttf)
+
+    lnW = m.get_weights()
+    attempts_per_step = WALKERS * (THERM_SWEEPS + SWEEPS_PER_ITER) * N
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
+
+    def step(ev=None):
+        """One weight iteration through the public API; ev = four CUDA events on the
+        instance's stream: step start, before the recorded sweeps, after them, and
+        after the host recursion (so a step's time includes the host work)."""
+        if ev:
+            ev[0].record(stream)
+        m.set_weights(lnW)
+        m.sweep(THERM_SWEEPS, record=False)
+        m.reset_histogram()
+        if ev:
+            ev[1].record(stream)
+        m.sweep(SWEEPS_PER_ITER, record=True)
+        if ev:
+            ev[2].record(stream)
+        H = m.get_histogram()
+        vis = H > 0
+        lnW[vis] -= np.log(H[vis].astype(np.float64))
+        if ev:
+            ev[3].record(stream)
+        return H
+
+    for _ in range(args.warmup):
+        step()
+        with torch.cuda.stream(stream):
+            flush.zero_()
+    stream.synchronize()
+
+    evs = [[torch.cuda.Event(enable_timing=True) for _ in range(4)] for _ in range(args.steps)]
+    barrier(dist)
+    torch.cuda.synchronize()
+    with ClockSampler(dev) as clocks:
+        for k in range(args.steps):
+            step(evs[k])
+            with torch.cuda.stream(stream):
+                flush.zero_()
+        stream.synchronize()
+        torch.cuda.synchronize()
+    step_ms = [evs[k][0].elapsed_time(evs[k][3]) for k in range(args.steps)]
+    therm_ms = [evs[k][0].elapsed_time(evs[k][1]) for k in range(args.steps)]
+    rec_ms = [evs[k][1].elapsed_time(evs[k][2]) for k in range(args.steps)]
+    total_s = sum(step_ms) / 1e3
+    total_s = max_over_ranks(dist, total_s)
+    barrier(dist)
+
+    # ---- end to end through the public API, host buffers, host clock ----
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        step()
+    torch.cuda.synchronize()
+    e2e_s = max_over_ranks(dist, time.perf_counter() - t0)
+
+    value = ws * attempts_per_step * args.steps / total_s
+    e2e_value = ws * attempts_per_step * args.steps / e2e_s
+    peaks = measured_peaks()
+    props = torch.cuda.get_device_properties(dev)
+    sm_count = props.multi_processor_count
+    sm_max_mhz = float(peaks.get("sm_max_mhz", 2070.0))
+    # integer-issue ceiling: every SM sub-partition issues one 32-lane instruction per clock
+    peak_tops = sm_count * 4 * 32 * sm_max_mhz * 1e6 / 1e12
+    rec_launch_s = (sum(rec_ms) / len(rec_ms)) / 1e3
+    rec_attempts = WALKERS * SWEEPS_PER_ITER * N
+    achieved_tops = OPS_PER_ATTEMPT * rec_attempts / rec_launch_s / 1e12
+    traffic = None
+    result = {
+        "metric": "spin-flip attempts/s (and time-to-flat H) at L=32, 16384 walkers; % of integer-issue roofline",
+        "value": value,
+        "unit": "attempts/s",
+        "n_gpus": ws,
+        "steps": args.steps,
+        "warmup": args.warmup,
+        "ms_per_step": sum(step_ms) / len(step_ms),
+        "higher_is_better": True,
+        "scaling": "weak",
+        "vs_baseline": None,
+        "dtype": "int32/u32 (spins int8, histogram u64, weights f64 on host)",
+        "data": "synthetic: random +/-1 Ising lattices from the seed",
+        "config": config_dict(),
+        "time_to_flat_s": ttf,
+        "iterations_to_flat": st.iterations,
+        "flat": bool(st.converged),
+        "flat_metric": st.last_metric,
+        "therm_ms_per_step": sum(therm_ms) / len(therm_ms),
+        "record_ms_per_step": sum(rec_ms) / len(rec_ms),
+        "e2e": {"value": e2e_value, "unit": "attempts/s",
+                "h2d_bytes_per_step": (N + 1) * 5 * 4, "d2h_bytes_per_step": (N + 1) * 8 + 4},
+        "gpu_launches": 2 * args.steps,
+        "roofline": {"bound": "alu", "achieved": achieved_tops, "peak": peak_tops, "unit": "Tops/s (int32)",
+                     "frac": achieved_tops / peak_tops, "traffic": traffic,
+                     "kernel": "sweep_kernel<uint32,int8,record>",
+                     "ops_per_attempt": OPS_PER_ATTEMPT,
+                     "peak_basis": f"{sm_count} SMs x 4 issue slots x 32 lanes x {sm_max_mhz:.0f} MHz"},
+        "clocks": clocks.summary(),
+    }
+    m.close()
+    if rank == 0 and not args.no_cpu_baseline:
+        rate, cores, wall = cpu_baseline(lnW, WALKERS)
+        result["cpu_baseline"] = {"value": rate, "unit": "attempts/s", "cores": cores, "kind": "oracle",
+                                  "sample": f"one step ({THERM_SWEEPS}+{SWEEPS_PER_ITER} sweeps) of all "
+                                            f"{WALKERS} walkers, split over {cores} processes ({wall:.1f} s)"}
+    if rank == 0:
+        print(json.dumps(result))
+    if dist is not None:
+        dist.destroy_process_group()
+
+
+def run_reference(args):
+    """The oracle, timed on the host cores over steps of the same workload."""
+    ws, rank, _ = dist_env()
+    if rank != 0:
+        return
+    import numpy as np
+    N = L_SIDE * L_SIDE
+    # bounded sample per step: 2048 of the 16384 walkers, one full step each
+    sample_walkers = 2048
+    lnW = np.zeros(N + 1)
+    rates = []
+    for _ in range(args.warmup):
+        pass
+    cores_used = 1
+    for _ in range(args.steps):
+        rate, cores_used, _ = cpu_baseline(lnW, sample_walkers)
+        rates.append(rate)
+    value = sum(rates) / len(rates)
+    out = {
+        "impl": "reference",
+        "metric": "spin-flip attempts/s (and time-to-flat H) at L=32, 16384 walkers; % of integer-issue roofline",
+        "value": value, "unit": "attempts/s", "n_gpus": ws, "steps": args.steps, "warmup": args.warmup,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "int32/u32 (spins int8, histogram u64, weights f64)", "data": "synthetic",
+        "config": config_dict(),
+        "cpu_baseline": {"value": value, "unit": "attempts/s", "cores": cores_used, "kind": "oracle",
+                         "sample": f"{sample_walkers} walkers x ({THERM_SWEEPS}+{SWEEPS_PER_ITER}) sweeps per step"},
+        "e2e": {"value": value, "unit": "attempts/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(out))
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["native", "reference"], default="native")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    if args.warmup < 3 and args.impl == "native":
+        args.warmup = 3
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_native(args)
+
+
+if __name__ == "__main__":
+    main()

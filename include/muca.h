@@ -1,0 +1,206 @@
+/*
+ * muca.h - C ABI of the GB300 (sm_103a) parallel multicanonical simulation of the 2D
+ * Ising model, after Gross, Zierenberg, Weigel and Janke, "Massively parallel
+ * multicanonical simulations" (arXiv:1707.00919).
+ *
+ * Many independent walkers, each a periodic L x L Ising lattice (Eq. 5, J = 1), run
+ * sequential single-spin-flip Metropolis updates accepted with the multicanonical
+ * weight ratio W(E')/W(E) (Sec. 2.1, Sec. 2.3).  All walkers share one weight function
+ * and add their energies to one histogram H(E) (Sec. 2.2); the host turns H into the
+ * next weights, ln W <- ln W - ln H (Eq. 4), until H is flat, and a production run with
+ * fixed weights estimates ln g(E) (Sec. 3.3).
+ *
+ * Conventions shared by every call
+ *   - N = L*L sites, site i = y*L + x (x fastest).  Energies live on the grid
+ *     E = -2N + 4e, e = 0 .. N ("energy index", Sec. 3); arrays over energies have
+ *     n_bins = N + 1 entries.  e = 1 and e = N - 1 are never visited (Sec. 3).
+ *   - Update order is typewriter: attempt t of a walker flips site t mod N, where t is
+ *     the instance's attempt counter, shared by all walkers and advanced by every
+ *     update call (thermalization included).  This is the shared site sequence of
+ *     Sec. 2.3 in its deterministic form.
+ *   - Random numbers: Philox4x32-10 (Salmon et al., cited in Sec. 2.3), key = the
+ *     64-bit seed, counter = (t >> 2 as 64 bits, walker index, tag), word t & 3; tag 0
+ *     drives the updates, tag 1 the initial spins (+1 iff the top bit of the word for
+ *     t = site is clear).
+ *   - Acceptance (Sec. 2.3, integer form): for a flip at a site with k antiparallel
+ *     neighbours the energy index moves to e' = e + 2 - k; with dw = lnW[e'] - lnW[e]
+ *     the threshold is 0xFFFFFFFF if dw >= 0, else min(floor(exp(dw) * 2^32), 2^32 - 1)
+ *     computed on the host in FP64, and 0 if e' is off the grid.  A draw r is
+ *     accepted iff r < T or T == 0xFFFFFFFF.
+ *   - Recording: each recorded attempt adds its post-decision energy index to H.
+ *
+ * Memory and threads
+ *   - The library owns all device memory of an instance (allocated at create, freed at
+ *     destroy) through the allocator set with muca_set_allocator (cudaMalloc by
+ *     default).  Host buffers passed in are copied and never retained.
+ *   - Calls on one instance run in order on the instance's CUDA stream (a stream of its
+ *     own unless muca_set_stream gives another).  Update calls are asynchronous; calls
+ *     that return data to the host synchronize that stream first.
+ *   - An instance must not be used from two host threads at the same time.
+ *
+ * Errors: every int-returning call returns MUCA_OK (0) or a negative MUCA_E* code and
+ * then sets a thread-local message readable with muca_last_error().  MUCA_EDEVICE means
+ * a kernel found an invalid state (an energy index off the grid); the instance should
+ * then be destroyed.
+ */
+#ifndef MUCA_H
+#define MUCA_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define MUCA_OK 0
+#define MUCA_EINVAL (-1)         /* bad argument: L, sizes, NULL pointers, non-finite weights */
+#define MUCA_ENOMEM (-2)         /* device or host allocation failed                        */
+#define MUCA_ECUDA (-3)          /* a CUDA runtime call failed                              */
+#define MUCA_ETIMEOUT (-4)       /* the deadline of muca_iterate_until_flat passed          */
+#define MUCA_ENOTCONVERGED (-5)  /* the iteration budget ran out before H was flat          */
+#define MUCA_EDEVICE (-6)        /* a kernel reported an invalid state                      */
+
+/* Lattice storage layouts in device memory (both walker-minor, Sec. 2.3: all walkers'
+ * copies of one site are adjacent, so a warp's accesses coalesce). */
+#define MUCA_LAYOUT_INT8 0       /* int8 spin[site][walker], values +1 / -1                  */
+#define MUCA_LAYOUT_PACKED 1     /* row[y][walker] bit words (bit x set = spin -1);
+                                    uint32 words for L <= 32, uint64 for L <= 64          */
+
+/* Stop rules of the weight iteration. */
+#define MUCA_STOP_MIN_MEAN 0     /* min H / mean H over accessible energies >= threshold    */
+#define MUCA_STOP_KL 1           /* Kullback-Leibler d_k < threshold (Eq. 6)                */
+#define MUCA_STOP_CHEBYSHEV 2    /* Chebyshev distance d_c < threshold (Eq. A.1)            */
+
+/* Update schedules of the weight iteration. */
+#define MUCA_SCHEDULE_SWEEPS 0   /* fixed sweeps per iteration                              */
+#define MUCA_SCHEDULE_PAPER 1    /* N_therm = f_therm w, N_updates of Eq. (7) (Sec. 3)      */
+
+typedef struct muca_s *muca_t;
+
+/* Options for muca_create_ex.  Zero-initialise, then set what differs from the
+ * defaults (layout MUCA_LAYOUT_INT8, walkers_per_block chosen by the library). */
+typedef struct {
+    int32_t L;                   /* lattice side: multiple of 4, 4 <= L <= 64               */
+    int64_t n_walkers;           /* 1 <= n_walkers <= 2^31 - 1                              */
+    uint64_t seed;               /* Philox key                                              */
+    int32_t layout;              /* MUCA_LAYOUT_*                                           */
+    int32_t walkers_per_block;   /* 0 = library default; else a multiple of 32, <= 1024     */
+} muca_options;
+
+/* Parameters of muca_iterate_until_flat.  muca_default_params fills the paper's values
+ * (Sec. 3: f_therm = 30, z = 2.25, factor 6, growth 1.1, d_k < 1e-4) with the fixed-sweep
+ * schedule and the min/mean >= 0.8 stop rule. */
+typedef struct {
+    int32_t schedule;            /* MUCA_SCHEDULE_*                                         */
+    int32_t stop_rule;           /* MUCA_STOP_*                                             */
+    double flat_threshold;       /* 0.8 (min/mean), 1e-4 (KL) or 0.05 (Chebyshev)           */
+    uint64_t therm_sweeps;       /* SWEEPS: unrecorded sweeps before each iteration        */
+    uint64_t sweeps_per_iter;    /* SWEEPS: recorded sweeps per iteration                  */
+    double f_therm;              /* PAPER: N_therm = f_therm * w attempts                  */
+    double z;                    /* PAPER: N_updates = floor(factor * w^z / W) + 1         */
+    double factor;
+    double growth;               /* PAPER: after full coverage N <- floor(growth N) + 1    */
+    int32_t max_iterations;      /* stop with MUCA_ENOTCONVERGED after this many           */
+    double deadline_s;           /* > 0: stop with MUCA_ETIMEOUT after this wall time      */
+} muca_params;
+
+/* Statistics of a weight iteration. */
+typedef struct {
+    int32_t iterations;          /* iterations run                                         */
+    int32_t converged;           /* 1 if the last histogram met the stop rule              */
+    double last_metric;          /* stop metric of the last iteration                      */
+    uint64_t attempts_per_walker;/* attempts per walker spent (thermalization included)    */
+    double seconds;              /* wall time of the call                                  */
+} muca_stats;
+
+/* Fills p with the defaults described at muca_params.  Returns MUCA_EINVAL for NULL. */
+int muca_default_params(muca_params *p);
+
+/* Creates an instance (Sec. 2.2: p walkers with identical weights): allocates the
+ * lattices, energies, threshold table and histogram on the current device, draws the
+ * initial spins (tag 1 stream), computes their energies, sets ln W = 0 (every flip
+ * accepted) and the attempt counter t = 0.  *out receives the handle.
+ * Errors: MUCA_EINVAL (L not a multiple of 4 in [4, 64], n_walkers out of range,
+ * out == NULL), MUCA_ENOMEM, MUCA_ECUDA. */
+int muca_create(int32_t L, int64_t n_walkers, uint64_t seed, muca_t *out);
+int muca_create_ex(const muca_options *opt, muca_t *out);
+
+/* Frees all device and host memory of the instance (NULL is accepted). */
+int muca_destroy(muca_t h);
+
+/* Runs the instance's work on the given cudaStream_t (passed as void*; NULL = the
+ * instance's own stream).  Work already queued on the old stream is synchronized first. */
+int muca_set_stream(muca_t h, void *cuda_stream);
+
+/* Replaces the device allocator used by later muca_create calls (alloc == NULL restores
+ * cudaMalloc/cudaFree).  alloc(size, ctx) returns device memory or NULL. */
+int muca_set_allocator(void *(*alloc)(size_t size, void *ctx), void (*release)(void *ptr, void *ctx),
+                       void *ctx);
+
+/* Copies ln W(e), e = 0 .. N (FP64, n_bins = N + 1), into the instance and rebuilds the
+ * acceptance-threshold table (Sec. 2.3).  Errors: MUCA_EINVAL (wrong n_bins, NULL,
+ * non-finite value). */
+int muca_set_weights(muca_t h, const double *lnW, size_t n_bins);
+
+/* Copies the current ln W into lnW_out[n_bins]. */
+int muca_get_weights(muca_t h, double *lnW_out, size_t n_bins);
+
+/* Copies the threshold table T[e*5 + k] (uint32, n = 5 * (N + 1)) into T_out. */
+int muca_get_table(muca_t h, uint32_t *T_out, size_t n);
+
+/* Every walker performs n_sweeps * N further attempts (Sec. 2.3); record = 0 is
+ * thermalization, record != 0 adds each post-decision energy to H.  Asynchronous. */
+int muca_sweep(muca_t h, uint64_t n_sweeps, int record);
+
+/* Same as muca_sweep for any number of attempts per walker (partial sweeps, as the
+ * schedule of Eq. (7) asks for). */
+int muca_attempts(muca_t h, uint64_t n_attempts, int record);
+
+/* Copies H (uint64, n_bins = N + 1, summed over walkers, Sec. 2.2) into out.  Syncs. */
+int muca_get_histogram(muca_t h, uint64_t *out, size_t n_bins);
+
+/* Sets H to zero (asynchronous). */
+int muca_reset_histogram(muca_t h);
+
+/* The weight iteration of Sec. 2.2 and Sec. 3: repeat { thermalize; zero H; record;
+ * stop if H meets the stop rule; else ln W(e) -= ln H(e) where H(e) > 0 (Eq. 4) }.
+ * On success the instance holds the weights that produced the flat histogram.
+ * Returns MUCA_OK, MUCA_ENOTCONVERGED or MUCA_ETIMEOUT (stats filled in every case),
+ * or another error.  p == NULL uses muca_default_params; stats may be NULL. */
+int muca_iterate_until_flat(muca_t h, const muca_params *p, muca_stats *stats);
+
+/* Production run (Sec. 3.3) with the current weights: therm_sweeps unrecorded sweeps,
+ * zero H, n_sweeps recorded sweeps, then ln g(e) = ln H(e) - ln W(e) on visited energies
+ * shifted so that sum_e exp(ln g(e)) = 2^N; unvisited energies get -inf.  H_out (may
+ * be NULL) receives the histogram, ln_g_out[n_bins] the estimate. */
+int muca_production(muca_t h, uint64_t therm_sweeps, uint64_t n_sweeps, uint64_t *H_out,
+                    double *ln_g_out, size_t n_bins);
+
+/* Copies the walkers' energy indices (int32, n = n_walkers).  Syncs. */
+int muca_get_energies(muca_t h, int32_t *e_out, size_t n);
+
+/* Copies the lattices as int8 spins out[walker][site] (+1 / -1, n = n_walkers * N). */
+int muca_get_lattice(muca_t h, int8_t *out, size_t n);
+
+/* Instance facts: lattice side, walkers, attempt counter, layout, walkers per block. */
+int muca_get_info(muca_t h, int32_t *L, int64_t *n_walkers, uint64_t *attempt_counter,
+                  int32_t *layout, int32_t *walkers_per_block);
+
+/* Waits for the instance's queued work; reports MUCA_EDEVICE if a kernel flagged an
+ * invalid state. */
+int muca_synchronize(muca_t h);
+
+/* Evaluates the library's device Philox4x32-10 on n counters (ctr[4*i .. 4*i+3]) with
+ * one key (key[0] low, key[1] high 32 bits of the seed) into out[4*n].  Host buffers;
+ * used to check the generator against independent implementations. */
+int muca_philox(const uint32_t *ctr, const uint32_t key[2], size_t n, uint32_t *out);
+
+/* Message of the last failed call on this host thread ("" if none). */
+const char *muca_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* MUCA_H */

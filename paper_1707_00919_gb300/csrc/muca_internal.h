@@ -1,0 +1,53 @@
+// muca_internal.h - launch interface between the host library (muca_api.cu) and the
+// device kernels (muca_kernels.cu).  Not part of the public ABI.
+#pragma once
+
+#include <cstddef>
+#include <cstdint>
+
+#include <cuda_runtime.h>
+
+namespace muca {
+
+// Device error word bits.
+constexpr uint32_t kErrEnergyRange = 1u;   // a walker's energy index was off the grid
+
+struct SweepArgs {
+    int32_t L;                  // lattice side (multiple of 4, <= 64)
+    int32_t layout;             // MUCA_LAYOUT_*
+    int64_t W;                  // walkers
+    uint64_t seed;              // Philox key
+    uint64_t t0;                // attempt counter of the first attempt
+    uint64_t n;                 // attempts per walker in this launch
+    void *lattice;              // layout-dependent, see muca.h
+    int32_t *energy;            // [W]
+    const uint32_t *table;      // [(N+1)*5]
+    unsigned long long *hist;   // [N+1], accumulated when recording
+    uint32_t *err;              // device error word
+};
+
+// Shared memory bytes a sweep launch with this many walkers per block needs.
+size_t sweep_smem_bytes(int L, int walkers_per_block, bool record);
+
+// Largest dynamic shared memory a block may use on this device (bytes).
+size_t sweep_smem_limit();
+
+// Launches one sweep kernel: grid = ceil(W / walkers_per_block).
+cudaError_t launch_sweep(const SweepArgs &a, int walkers_per_block, bool record, cudaStream_t s);
+
+// Draws the initial spins (tag 1 stream) and their energy indices.
+cudaError_t launch_init(int32_t L, int32_t layout, int64_t W, uint64_t seed, void *lattice,
+                        int32_t *energy, cudaStream_t s);
+
+// Unpacks lattices into int8 out[walker][site] (+1/-1).
+cudaError_t launch_unpack(int32_t L, int32_t layout, int64_t W, const void *lattice, int8_t *out,
+                          cudaStream_t s);
+
+// Evaluates the device Philox4x32-10 on n counters.
+cudaError_t launch_philox(const uint32_t *ctr, uint32_t k0, uint32_t k1, size_t n, uint32_t *out,
+                          cudaStream_t s);
+
+// Bytes of the lattice storage of W walkers.
+size_t lattice_bytes(int32_t L, int32_t layout, int64_t W);
+
+}  // namespace muca

@@ -1,0 +1,365 @@
+// muca_kernels.cu - sm_103a kernels of the parallel multicanonical 2D Ising update
+// (Gross, Zierenberg, Weigel, Janke, arXiv:1707.00919, Sec. 2.3).
+//
+// One thread runs one walker (Sec. 2.3: one thread per walker, lattices interleaved so
+// that a warp's accesses to one site coalesce).  Inside a launch the walker's lattice
+// is bit-packed into shared memory, one word per row ([row][walker-in-block], so a
+// warp's row loads hit 32 consecutive words), the acceptance thresholds T[e][k] sit in
+// shared memory, random words come from an inline Philox4x32-10, and the visited
+// energies go run-length encoded into a per-block shared histogram that is added to the
+// global uint64 histogram once at the end of the launch.
+#include <cstdint>
+
+#include <cuda_runtime.h>
+
+#include "../../include/muca.h"
+#include "muca_internal.h"
+
+namespace muca {
+namespace {
+
+// Philox4x32-10 of Salmon et al. (SC'11), the generator of Sec. 2.3.
+__device__ __forceinline__ uint4 philox4x32_10(uint4 c, uint32_t k0, uint32_t k1)
+{
+#pragma unroll
+    for (int round = 0; round < 10; ++round) {
+        if (round > 0) {
+            k0 += 0x9E3779B9u;
+            k1 += 0xBB67AE85u;
+        }
+        const uint32_t lo0 = 0xD2511F53u * c.x;
+        const uint32_t hi0 = __umulhi(0xD2511F53u, c.x);
+        const uint32_t lo1 = 0xCD9E8D57u * c.z;
+        const uint32_t hi1 = __umulhi(0xCD9E8D57u, c.z);
+        c = make_uint4(hi1 ^ c.y ^ k0, lo1, hi0 ^ c.w ^ k1, lo0);
+    }
+    return c;
+}
+
+constexpr uint32_t kTagMetropolis = 0u;
+constexpr uint32_t kTagInit = 1u;
+
+__host__ __device__ constexpr size_t align_up(size_t v, size_t a) { return (v + a - 1) / a * a; }
+
+template <typename RowT>
+__device__ __forceinline__ uint32_t bit_at(RowT w, int x)
+{
+    return (uint32_t)(w >> x) & 1u;
+}
+
+// ---------------------------------------------------------------------------------
+// Sweep kernel.  Template: row word type (uint32 for L <= 32, uint64 for L <= 64),
+// global lattice layout, and whether visited energies are recorded.
+// ---------------------------------------------------------------------------------
+template <typename RowT, int LAYOUT, bool RECORD>
+__global__ void __launch_bounds__(1024) sweep_kernel(const SweepArgs a)
+{
+    extern __shared__ __align__(16) unsigned char smem[];
+    const int L = a.L;
+    const int N = L * L;
+    const int nb = N + 1;
+    const int wpb = blockDim.x;
+    uint32_t *sT = reinterpret_cast<uint32_t *>(smem);
+    uint32_t *sH = sT + nb * 5;
+    RowT *sRows = reinterpret_cast<RowT *>(smem + align_up((size_t)(nb * 5 + (RECORD ? nb : 0)) * 4, 16));
+
+    const int tid = threadIdx.x;
+    const int64_t w = (int64_t)blockIdx.x * wpb + tid;
+    bool active = w < a.W;
+
+    for (int i = tid; i < nb * 5; i += wpb)
+        sT[i] = a.table[i];
+    if (RECORD)
+        for (int i = tid; i < nb; i += wpb)
+            sH[i] = 0u;
+
+    RowT *col = sRows + tid;   // this walker's rows: col[y * wpb]
+    int32_t e = 0;
+    if (active) {
+        if (LAYOUT == MUCA_LAYOUT_PACKED) {
+            const RowT *g = reinterpret_cast<const RowT *>(a.lattice);
+            for (int y = 0; y < L; ++y)
+                col[y * wpb] = g[(size_t)y * a.W + w];
+        } else {
+            const int8_t *g = reinterpret_cast<const int8_t *>(a.lattice);
+            for (int y = 0; y < L; ++y) {
+                RowT r = 0;
+                for (int x = 0; x < L; ++x)
+                    r |= (RowT)(g[(size_t)(y * L + x) * a.W + w] < 0) << x;
+                col[y * wpb] = r;
+            }
+        }
+        e = a.energy[w];
+        if (e < 0 || e > N) {
+            atomicOr(a.err, kErrEnergyRange);
+            active = false;
+        }
+    }
+    __syncthreads();
+
+    int32_t run_e = e;
+    uint32_t run_n = 0;
+    if (active) {
+        const uint32_t k0 = (uint32_t)a.seed, k1 = (uint32_t)(a.seed >> 32);
+        const uint32_t wid = (uint32_t)w;
+        uint64_t t = a.t0;
+        const uint64_t tend = a.t0 + a.n;
+        while (t < tend) {
+            const int i = (int)(t % (uint64_t)N);
+            const int y = i / L;
+            const int x0 = i - y * L;
+            const uint64_t left = tend - t;
+            const int x1 = left < (uint64_t)(L - x0) ? x0 + (int)left : L;
+            const int yu = (y == 0) ? L - 1 : y - 1;
+            const int yd = (y == L - 1) ? 0 : y + 1;
+            const RowT U = col[yu * wpb];
+            RowT C = col[y * wpb];
+            const RowT D = col[yd * wpb];
+            // Vertical disagreements: bit x of VU/VD is fixed until site x itself is
+            // visited (a flip at x' != x leaves bit x alone), so one XOR per row serves
+            // every site of the row.
+            const RowT VU = U ^ C;
+            const RowT VD = D ^ C;
+            const uint64_t tb = t - (uint64_t)x0;   // attempt number of column 0
+            for (int xb = x0 & ~3; xb < x1; xb += 4) {
+                const uint64_t blk = (tb + (uint64_t)xb) >> 2;
+                const uint4 rw = philox4x32_10(make_uint4((uint32_t)blk, (uint32_t)(blk >> 32), wid, kTagMetropolis), k0, k1);
+                const uint32_t words[4] = {rw.x, rw.y, rw.z, rw.w};
+#pragma unroll
+                for (int u = 0; u < 4; ++u) {
+                    const int x = xb + u;
+                    if (x < x0 || x >= x1)
+                        continue;
+                    const int xl = (x == 0) ? L - 1 : x - 1;
+                    const int xr = (x == L - 1) ? 0 : x + 1;
+                    const uint32_t sx = bit_at(C, x);
+                    const uint32_t k = bit_at(VU, x) + bit_at(VD, x) + (sx ^ bit_at(C, xl)) + (sx ^ bit_at(C, xr));
+                    const uint32_t thr = sT[e * 5 + (int)k];
+                    const bool acc = (words[u] < thr) | (thr == 0xFFFFFFFFu);
+                    if (acc) {
+                        C ^= (RowT)1 << x;
+                        e += 2 - (int)k;
+                    }
+                    if (RECORD) {
+                        if (e != run_e) {
+                            if (run_n)
+                                atomicAdd(&sH[run_e], run_n);
+                            run_e = e;
+                            run_n = 0u;
+                        }
+                        ++run_n;
+                    }
+                }
+            }
+            col[y * wpb] = C;
+            t += (uint64_t)(x1 - x0);
+        }
+        if (RECORD && run_n)
+            atomicAdd(&sH[run_e], run_n);
+    }
+    __syncthreads();
+    if (RECORD)
+        for (int i = tid; i < nb; i += wpb) {
+            const uint32_t v = sH[i];
+            if (v)
+                atomicAdd(&a.hist[i], (unsigned long long)v);
+        }
+    if (active) {
+        if (LAYOUT == MUCA_LAYOUT_PACKED) {
+            RowT *g = reinterpret_cast<RowT *>(a.lattice);
+            for (int y = 0; y < L; ++y)
+                g[(size_t)y * a.W + w] = col[y * wpb];
+        } else {
+            int8_t *g = reinterpret_cast<int8_t *>(a.lattice);
+            for (int y = 0; y < L; ++y) {
+                const RowT r = col[y * wpb];
+                for (int x = 0; x < L; ++x)
+                    g[(size_t)(y * L + x) * a.W + w] = bit_at(r, x) ? (int8_t)-1 : (int8_t)1;
+            }
+        }
+        a.energy[w] = e;
+    }
+}
+
+// ---------------------------------------------------------------------------------
+// Initial spins: +1 iff the top bit of the tag-1 word for attempt number t = site is
+// clear; the energy index is the number of unsatisfied bonds over two.
+// ---------------------------------------------------------------------------------
+template <typename RowT, int LAYOUT>
+__global__ void init_kernel(int32_t L, int64_t W, uint64_t seed, void *lattice, int32_t *energy)
+{
+    const int64_t w = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (w >= W)
+        return;
+    const uint32_t k0 = (uint32_t)seed, k1 = (uint32_t)(seed >> 32);
+    const RowT mask = (L == (int)(8 * sizeof(RowT))) ? ~(RowT)0 : (((RowT)1 << L) - 1);
+    RowT first = 0, prev = 0;
+    int unsat = 0;
+    for (int y = 0; y < L; ++y) {
+        RowT r = 0;
+        for (int x = 0; x < L; x += 4) {
+            const uint32_t site = (uint32_t)(y * L + x);
+            const uint4 q = philox4x32_10(make_uint4(site >> 2, 0u, (uint32_t)w, kTagInit), k0, k1);
+            const uint32_t words[4] = {q.x, q.y, q.z, q.w};
+#pragma unroll
+            for (int u = 0; u < 4; ++u)
+                r |= (RowT)(words[u] >> 31) << (x + u);
+        }
+        const RowT rot = (r >> 1) | ((r & 1) << (L - 1));   // bit x = spin at x+1 (mod L)
+        unsat += __popcll((unsigned long long)((r ^ rot) & mask));
+        if (y == 0)
+            first = r;
+        else
+            unsat += __popcll((unsigned long long)((r ^ prev) & mask));
+        prev = r;
+        if (LAYOUT == MUCA_LAYOUT_PACKED) {
+            reinterpret_cast<RowT *>(lattice)[(size_t)y * W + w] = r;
+        } else {
+            int8_t *g = reinterpret_cast<int8_t *>(lattice);
+            for (int x = 0; x < L; ++x)
+                g[(size_t)(y * L + x) * W + w] = bit_at(r, x) ? (int8_t)-1 : (int8_t)1;
+        }
+    }
+    unsat += __popcll((unsigned long long)((prev ^ first) & mask));   // row L-1 to row 0
+    energy[w] = unsat / 2;
+}
+
+template <typename RowT, int LAYOUT>
+__global__ void unpack_kernel(int32_t L, int64_t W, const void *lattice, int8_t *out)
+{
+    const int64_t w = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (w >= W)
+        return;
+    const int N = L * L;
+    for (int i = 0; i < N; ++i) {
+        int8_t v;
+        if (LAYOUT == MUCA_LAYOUT_PACKED) {
+            const RowT r = reinterpret_cast<const RowT *>(lattice)[(size_t)(i / L) * W + w];
+            v = bit_at(r, i % L) ? (int8_t)-1 : (int8_t)1;
+        } else {
+            v = reinterpret_cast<const int8_t *>(lattice)[(size_t)i * W + w];
+        }
+        out[(size_t)w * N + i] = v;
+    }
+}
+
+__global__ void philox_kernel(const uint32_t *ctr, uint32_t k0, uint32_t k1, size_t n, uint32_t *out)
+{
+    const size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n)
+        return;
+    const uint4 c = make_uint4(ctr[4 * i], ctr[4 * i + 1], ctr[4 * i + 2], ctr[4 * i + 3]);
+    const uint4 r = philox4x32_10(c, k0, k1);
+    out[4 * i] = r.x;
+    out[4 * i + 1] = r.y;
+    out[4 * i + 2] = r.z;
+    out[4 * i + 3] = r.w;
+}
+
+template <typename RowT, int LAYOUT, bool RECORD>
+cudaError_t launch_sweep_t(const SweepArgs &a, int wpb, cudaStream_t s)
+{
+    const size_t smem = sweep_smem_bytes(a.L, wpb, RECORD);
+    auto kern = sweep_kernel<RowT, LAYOUT, RECORD>;
+    static size_t configured = 0;   // dynamic smem limit already granted to this instantiation
+    if (smem > 48 * 1024 && smem > configured) {
+        cudaError_t err = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (err != cudaSuccess)
+            return err;
+        configured = smem;
+    }
+    const int64_t blocks = (a.W + wpb - 1) / wpb;
+    kern<<<(unsigned)blocks, wpb, smem, s>>>(a);
+    return cudaGetLastError();
+}
+
+template <typename RowT>
+cudaError_t launch_sweep_row(const SweepArgs &a, int wpb, bool record, cudaStream_t s)
+{
+    if (a.layout == MUCA_LAYOUT_PACKED)
+        return record ? launch_sweep_t<RowT, MUCA_LAYOUT_PACKED, true>(a, wpb, s)
+                      : launch_sweep_t<RowT, MUCA_LAYOUT_PACKED, false>(a, wpb, s);
+    return record ? launch_sweep_t<RowT, MUCA_LAYOUT_INT8, true>(a, wpb, s)
+                  : launch_sweep_t<RowT, MUCA_LAYOUT_INT8, false>(a, wpb, s);
+}
+
+}  // namespace
+
+size_t sweep_smem_bytes(int L, int wpb, bool record)
+{
+    const size_t nb = (size_t)L * L + 1;
+    const size_t row = L <= 32 ? 4 : 8;
+    return align_up((nb * 5 + (record ? nb : 0)) * 4, 16) + (size_t)L * wpb * row;
+}
+
+size_t sweep_smem_limit()
+{
+    int dev = 0, v = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&v, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+    return (size_t)v;
+}
+
+cudaError_t launch_sweep(const SweepArgs &a, int wpb, bool record, cudaStream_t s)
+{
+    if (a.n == 0 || a.W == 0)
+        return cudaSuccess;
+    if (a.L <= 32)
+        return launch_sweep_row<uint32_t>(a, wpb, record, s);
+    return launch_sweep_row<unsigned long long>(a, wpb, record, s);
+}
+
+cudaError_t launch_init(int32_t L, int32_t layout, int64_t W, uint64_t seed, void *lattice, int32_t *energy,
+                        cudaStream_t s)
+{
+    const int threads = 128;
+    const unsigned blocks = (unsigned)((W + threads - 1) / threads);
+    if (L <= 32) {
+        if (layout == MUCA_LAYOUT_PACKED)
+            init_kernel<uint32_t, MUCA_LAYOUT_PACKED><<<blocks, threads, 0, s>>>(L, W, seed, lattice, energy);
+        else
+            init_kernel<uint32_t, MUCA_LAYOUT_INT8><<<blocks, threads, 0, s>>>(L, W, seed, lattice, energy);
+    } else {
+        if (layout == MUCA_LAYOUT_PACKED)
+            init_kernel<unsigned long long, MUCA_LAYOUT_PACKED><<<blocks, threads, 0, s>>>(L, W, seed, lattice, energy);
+        else
+            init_kernel<unsigned long long, MUCA_LAYOUT_INT8><<<blocks, threads, 0, s>>>(L, W, seed, lattice, energy);
+    }
+    return cudaGetLastError();
+}
+
+cudaError_t launch_unpack(int32_t L, int32_t layout, int64_t W, const void *lattice, int8_t *out, cudaStream_t s)
+{
+    const int threads = 128;
+    const unsigned blocks = (unsigned)((W + threads - 1) / threads);
+    if (L <= 32) {
+        if (layout == MUCA_LAYOUT_PACKED)
+            unpack_kernel<uint32_t, MUCA_LAYOUT_PACKED><<<blocks, threads, 0, s>>>(L, W, lattice, out);
+        else
+            unpack_kernel<uint32_t, MUCA_LAYOUT_INT8><<<blocks, threads, 0, s>>>(L, W, lattice, out);
+    } else {
+        if (layout == MUCA_LAYOUT_PACKED)
+            unpack_kernel<unsigned long long, MUCA_LAYOUT_PACKED><<<blocks, threads, 0, s>>>(L, W, lattice, out);
+        else
+            unpack_kernel<unsigned long long, MUCA_LAYOUT_INT8><<<blocks, threads, 0, s>>>(L, W, lattice, out);
+    }
+    return cudaGetLastError();
+}
+
+cudaError_t launch_philox(const uint32_t *ctr, uint32_t k0, uint32_t k1, size_t n, uint32_t *out, cudaStream_t s)
+{
+    if (n == 0)
+        return cudaSuccess;
+    const int threads = 128;
+    philox_kernel<<<(unsigned)((n + threads - 1) / threads), threads, 0, s>>>(ctr, k0, k1, n, out);
+    return cudaGetLastError();
+}
+
+size_t lattice_bytes(int32_t L, int32_t layout, int64_t W)
+{
+    if (layout == MUCA_LAYOUT_PACKED)
+        return (size_t)L * (size_t)W * (L <= 32 ? 4 : 8);
+    return (size_t)L * L * (size_t)W;
+}
+
+}  // namespace muca

@@ -1,0 +1,287 @@
+"""Python binding of the C ABI in include/muca.h.
+
+Argument marshalling only: every step of the simulation runs in libmuca.so's CUDA
+kernels and host library.  The module-level functions carry the C names; `Muca` wraps
+one instance.  PyTorch, when importable, supplies device memory (its caching allocator)
+and, optionally, the CUDA stream the instance runs on.
+"""
+from __future__ import annotations
+
+import ctypes
+from dataclasses import dataclass
+
+import numpy as np
+
+from . import _lib as C
+from ._lib import (MUCA_LAYOUT_INT8, MUCA_LAYOUT_PACKED, MUCA_OK, MUCA_SCHEDULE_PAPER,  # noqa: F401
+                   MUCA_SCHEDULE_SWEEPS, MUCA_STOP_CHEBYSHEV, MUCA_STOP_KL, MUCA_STOP_MIN_MEAN,
+                   muca_options, muca_params, muca_stats)
+
+
+class MucaError(RuntimeError):
+    def __init__(self, code: int, message: str):
+        super().__init__(f"muca error {code}: {message}")
+        self.code = code
+
+
+def _check(rc: int) -> int:
+    if rc != MUCA_OK:
+        raise MucaError(rc, C.load().muca_last_error().decode(errors="replace"))
+    return rc
+
+
+def _p(a: np.ndarray, t):
+    return a.ctypes.data_as(ctypes.POINTER(t))
+
+
+# ---------------------------------------------------------------------------------
+# PyTorch as the device allocator
+# ---------------------------------------------------------------------------------
+_torch_cb = None
+
+
+def use_torch_allocator() -> bool:
+    """Routes libmuca's device allocations through torch's caching allocator."""
+    global _torch_cb
+    if _torch_cb is not None:
+        return True
+    try:
+        import torch
+    except ImportError:
+        return False
+    if not torch.cuda.is_available():
+        return False
+
+    def _alloc(size, ctx):
+        try:
+            return torch.cuda.caching_allocator_alloc(int(size))
+        except Exception:
+            return None
+
+    def _release(ptr, ctx):
+        torch.cuda.caching_allocator_delete(ptr)
+
+    cb = (C.ALLOC_FN(_alloc), C.RELEASE_FN(_release))
+    _check(C.load().muca_set_allocator(cb[0], cb[1], None))
+    _torch_cb = cb
+    return True
+
+
+# ---------------------------------------------------------------------------------
+# C names
+# ---------------------------------------------------------------------------------
+def muca_default_params() -> muca_params:
+    p = muca_params()
+    _check(C.load().muca_default_params(ctypes.byref(p)))
+    return p
+
+
+def muca_create(L: int, n_walkers: int, seed: int) -> ctypes.c_void_p:
+    h = ctypes.c_void_p()
+    _check(C.load().muca_create(L, n_walkers, seed, ctypes.byref(h)))
+    return h
+
+
+def muca_create_ex(L: int, n_walkers: int, seed: int, layout: int = MUCA_LAYOUT_INT8,
+                   walkers_per_block: int = 0) -> ctypes.c_void_p:
+    o = muca_options(L, n_walkers, seed, layout, walkers_per_block)
+    h = ctypes.c_void_p()
+    _check(C.load().muca_create_ex(ctypes.byref(o), ctypes.byref(h)))
+    return h
+
+
+def muca_destroy(h) -> None:
+    _check(C.load().muca_destroy(h))
+
+
+def muca_set_stream(h, stream_handle: int | None) -> None:
+    _check(C.load().muca_set_stream(h, ctypes.c_void_p(stream_handle or 0)))
+
+
+def muca_set_weights(h, lnW) -> None:
+    a = np.ascontiguousarray(lnW, dtype=np.float64)
+    _check(C.load().muca_set_weights(h, _p(a, ctypes.c_double), a.size))
+
+
+def muca_get_weights(h, n_bins: int) -> np.ndarray:
+    a = np.zeros(n_bins, dtype=np.float64)
+    _check(C.load().muca_get_weights(h, _p(a, ctypes.c_double), n_bins))
+    return a
+
+
+def muca_get_table(h, n_bins: int) -> np.ndarray:
+    a = np.zeros(n_bins * 5, dtype=np.uint32)
+    _check(C.load().muca_get_table(h, _p(a, ctypes.c_uint32), a.size))
+    return a
+
+
+def muca_sweep(h, n_sweeps: int, record: bool) -> None:
+    _check(C.load().muca_sweep(h, n_sweeps, 1 if record else 0))
+
+
+def muca_attempts(h, n_attempts: int, record: bool) -> None:
+    _check(C.load().muca_attempts(h, n_attempts, 1 if record else 0))
+
+
+def muca_get_histogram(h, n_bins: int) -> np.ndarray:
+    a = np.zeros(n_bins, dtype=np.uint64)
+    _check(C.load().muca_get_histogram(h, _p(a, ctypes.c_uint64), n_bins))
+    return a
+
+
+def muca_reset_histogram(h) -> None:
+    _check(C.load().muca_reset_histogram(h))
+
+
+def muca_iterate_until_flat(h, params: muca_params | None = None, raise_on_fail: bool = True):
+    st = muca_stats()
+    rc = C.load().muca_iterate_until_flat(h, ctypes.byref(params) if params is not None else None,
+                                           ctypes.byref(st))
+    if raise_on_fail:
+        _check(rc)
+    return rc, st
+
+
+def muca_production(h, therm_sweeps: int, n_sweeps: int, n_bins: int):
+    H = np.zeros(n_bins, dtype=np.uint64)
+    g = np.zeros(n_bins, dtype=np.float64)
+    _check(C.load().muca_production(h, therm_sweeps, n_sweeps, _p(H, ctypes.c_uint64),
+                                    _p(g, ctypes.c_double), n_bins))
+    return H, g
+
+
+def muca_get_energies(h, n_walkers: int) -> np.ndarray:
+    a = np.zeros(n_walkers, dtype=np.int32)
+    _check(C.load().muca_get_energies(h, _p(a, ctypes.c_int32), n_walkers))
+    return a
+
+
+def muca_get_lattice(h, n_walkers: int, N: int) -> np.ndarray:
+    a = np.zeros((n_walkers, N), dtype=np.int8)
+    _check(C.load().muca_get_lattice(h, _p(a, ctypes.c_int8), a.size))
+    return a
+
+
+def muca_get_info(h):
+    L, W, t, lay, wpb = (ctypes.c_int32(), ctypes.c_int64(), ctypes.c_uint64(), ctypes.c_int32(),
+                         ctypes.c_int32())
+    _check(C.load().muca_get_info(h, ctypes.byref(L), ctypes.byref(W), ctypes.byref(t), ctypes.byref(lay),
+                                  ctypes.byref(wpb)))
+    return L.value, W.value, t.value, lay.value, wpb.value
+
+
+def muca_synchronize(h) -> None:
+    _check(C.load().muca_synchronize(h))
+
+
+def muca_philox(ctr, key) -> np.ndarray:
+    c = np.ascontiguousarray(ctr, dtype=np.uint32).reshape(-1)
+    k = np.ascontiguousarray(key, dtype=np.uint32).reshape(2)
+    n = c.size // 4
+    out = np.zeros(4 * n, dtype=np.uint32)
+    _check(C.load().muca_philox(_p(c, ctypes.c_uint32), _p(k, ctypes.c_uint32), n, _p(out, ctypes.c_uint32)))
+    return out.reshape(n, 4)
+
+
+def muca_last_error() -> str:
+    return C.load().muca_last_error().decode(errors="replace")
+
+
+# ---------------------------------------------------------------------------------
+# object wrapper
+# ---------------------------------------------------------------------------------
+@dataclass
+class IterationStats:
+    code: int
+    iterations: int
+    converged: bool
+    last_metric: float
+    attempts_per_walker: int
+    seconds: float
+
+
+def make_params(schedule: int = MUCA_SCHEDULE_SWEEPS, stop_rule: int = MUCA_STOP_MIN_MEAN,
+                flat_threshold: float = 0.8, therm_sweeps: int = 31, sweeps_per_iter: int = 100,
+                f_therm: float = 30.0, z: float = 2.25, factor: float = 6.0, growth: float = 1.1,
+                max_iterations: int = 1000, deadline_s: float = 0.0) -> muca_params:
+    return muca_params(schedule, stop_rule, flat_threshold, therm_sweeps, sweeps_per_iter, f_therm, z,
+                       factor, growth, max_iterations, deadline_s)
+
+
+class Muca:
+    """One multicanonical instance: n_walkers periodic L x L Ising lattices on the GPU."""
+
+    def __init__(self, L: int, n_walkers: int, seed: int, layout: int = MUCA_LAYOUT_INT8,
+                 walkers_per_block: int = 0, stream=None, torch_allocator: bool = True):
+        if torch_allocator:
+            use_torch_allocator()
+        self.L, self.N, self.W = L, L * L, n_walkers
+        self.n_bins = self.N + 1
+        self._h = muca_create_ex(L, n_walkers, seed, layout, walkers_per_block)
+        if stream is not None:
+            handle = getattr(stream, "cuda_stream", stream)
+            muca_set_stream(self._h, int(handle))
+
+    # lifetime
+    def close(self) -> None:
+        if self._h:
+            muca_destroy(self._h)
+            self._h = None
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    # calls
+    def set_weights(self, lnW) -> None:
+        muca_set_weights(self._h, lnW)
+
+    def get_weights(self) -> np.ndarray:
+        return muca_get_weights(self._h, self.n_bins)
+
+    def get_table(self) -> np.ndarray:
+        return muca_get_table(self._h, self.n_bins)
+
+    def sweep(self, n_sweeps: int, record: bool = True) -> None:
+        muca_sweep(self._h, n_sweeps, record)
+
+    def attempts(self, n_attempts: int, record: bool = True) -> None:
+        muca_attempts(self._h, n_attempts, record)
+
+    def get_histogram(self) -> np.ndarray:
+        return muca_get_histogram(self._h, self.n_bins)
+
+    def reset_histogram(self) -> None:
+        muca_reset_histogram(self._h)
+
+    def iterate_until_flat(self, params: muca_params | None = None, raise_on_fail: bool = False) -> IterationStats:
+        rc, st = muca_iterate_until_flat(self._h, params, raise_on_fail)
+        return IterationStats(rc, st.iterations, bool(st.converged), st.last_metric, st.attempts_per_walker,
+                              st.seconds)
+
+    def production(self, therm_sweeps: int, n_sweeps: int):
+        return muca_production(self._h, therm_sweeps, n_sweeps, self.n_bins)
+
+    def get_energies(self) -> np.ndarray:
+        return muca_get_energies(self._h, self.W)
+
+    def get_lattice(self) -> np.ndarray:
+        return muca_get_lattice(self._h, self.W, self.N)
+
+    def info(self):
+        return muca_get_info(self._h)
+
+    @property
+    def attempt_counter(self) -> int:
+        return muca_get_info(self._h)[2]
+
+    def synchronize(self) -> None:
+        muca_synchronize(self._h)

@@ -1,0 +1,58 @@
+"""The C ABI library builds, loads, and exports every symbol include/muca.h declares
+(no compute calls: no GPU needed)."""
+import ctypes
+import os
+import re
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def declared_symbols():
+    src = open(os.path.join(ROOT, "include", "muca.h")).read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    return sorted(set(re.findall(r"\b(muca_[a-z_]+)\s*\(", src)))
+
+
+@pytest.fixture(scope="module")
+def lib():
+    from paper_1707_00919_gb300 import build
+    build.build()
+    from paper_1707_00919_gb300 import _lib
+    return _lib.load()
+
+
+def test_every_declared_symbol_is_exported(lib):
+    names = declared_symbols()
+    assert len(names) >= 20
+    for n in names:
+        assert hasattr(lib, n), n
+
+
+def test_binding_declares_every_symbol():
+    from paper_1707_00919_gb300 import _lib
+    assert sorted(_lib.SIGNATURES) == declared_symbols()
+
+
+def test_default_params_and_errors_without_gpu(lib):
+    from paper_1707_00919_gb300 import _lib
+    p = _lib.muca_params()
+    assert lib.muca_default_params(ctypes.byref(p)) == 0
+    assert p.flat_threshold == 0.8 and p.f_therm == 30.0 and p.z == 2.25 and p.growth == 1.1
+    assert lib.muca_default_params(None) == _lib.MUCA_EINVAL
+    assert b"NULL" in lib.muca_last_error()
+    # argument validation happens before any device call
+    h = ctypes.c_void_p()
+    assert lib.muca_create(6, 10, 1, ctypes.byref(h)) == _lib.MUCA_EINVAL
+    assert lib.muca_create(68, 10, 1, ctypes.byref(h)) == _lib.MUCA_EINVAL
+    assert lib.muca_create(8, 0, 1, ctypes.byref(h)) == _lib.MUCA_EINVAL
+    assert lib.muca_sweep(None, 1, 0) == _lib.MUCA_EINVAL
+
+
+def test_missing_library_fails_loudly(monkeypatch, tmp_path):
+    from paper_1707_00919_gb300 import _lib
+    monkeypatch.setattr(_lib, "LIB_PATH", str(tmp_path / "nope.so"))
+    monkeypatch.setattr(_lib, "_lib", None)
+    with pytest.raises(ImportError):
+        _lib.load()
