@@ -85,7 +85,7 @@ typedef struct {
     int64_t n_walkers;           /* 1 <= n_walkers <= 2^31 - 1                              */
     uint64_t seed;               /* Philox key                                              */
     int32_t layout;              /* MUCA_LAYOUT_*                                           */
-    int32_t walkers_per_block;   /* 0 = library default; else a multiple of 32, <= 1024     */
+    int32_t walkers_per_block;   /* 0 = library default; else a multiple of 32, <= 256      */
 } muca_options;
 
 /* Parameters of muca_iterate_until_flat.  muca_default_params fills the paper's values

@@ -330,9 +330,9 @@ int muca_create_ex(const muca_options *opt, muca_t *out)
     int32_t wpb = opt->walkers_per_block;
     if (wpb == 0)
         wpb = 64;
-    if (wpb < 32 || wpb > 1024 || wpb % 32 != 0)
-        return fail(MUCA_EINVAL, "walkers_per_block = %d: must be a multiple of 32 in [32, 1024]", wpb);
-    const size_t smem = muca::sweep_smem_bytes(L, wpb, true);
+    if (wpb < 32 || wpb > 256 || wpb % 32 != 0)
+        return fail(MUCA_EINVAL, "walkers_per_block = %d: must be a multiple of 32 in [32, 256]", wpb);
+    const size_t smem = std::max(muca::sweep_smem_bytes(L, wpb, true), muca::full_smem_bytes(L, wpb, true));
     if (smem > muca::sweep_smem_limit())
         return fail(MUCA_EINVAL, "L = %d with %d walkers per block needs %zu bytes of shared memory", L, wpb,
                     smem);

@@ -29,11 +29,20 @@ struct SweepArgs {
 // Shared memory bytes a sweep launch with this many walkers per block needs.
 size_t sweep_smem_bytes(int L, int walkers_per_block, bool record);
 
+// Shared memory bytes of the whole-sweep kernel (eight thresholds per energy).
+size_t full_smem_bytes(int L, int walkers_per_block, bool record);
+
 // Largest dynamic shared memory a block may use on this device (bytes).
 size_t sweep_smem_limit();
 
-// Launches one sweep kernel: grid = ceil(W / walkers_per_block).
+// Runs attempts [t0, t0 + n) of every walker: whole sweeps go to the kernel specialised
+// for L (L in {8, 16, 24, 32, 48, 64}), partial sweeps and other L to the generic kernel.
+// Grid = ceil(W / walkers_per_block) per launch.
 cudaError_t launch_sweep(const SweepArgs &a, int walkers_per_block, bool record, cudaStream_t s);
+
+// Routes whole sweeps to the generic kernel when false (used by tests that compare the
+// two kernels).
+void set_full_kernel_enabled(bool on);
 
 // Draws the initial spins (tag 1 stream) and their energy indices.
 cudaError_t launch_init(int32_t L, int32_t layout, int64_t W, uint64_t seed, void *lattice,
