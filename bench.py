@@ -104,7 +104,7 @@ class ClockSampler:
         try:
             self.proc = subprocess.Popen(
                 ["nvidia-smi", "-i", str(self.dev), f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
-                 "-lms", "100"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+                 "-lms", "50"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
             self.thread = threading.Thread(target=self._read, daemon=True)
             self.thread.start()
         except (OSError, ValueError):
@@ -142,6 +142,36 @@ class ClockSampler:
             return {"sm_mhz": None, "sm_max_mhz": mx, "reasons": [], "samples": 0}
         sm.sort()
         return {"sm_mhz": sm[len(sm) // 2], "sm_max_mhz": mx, "reasons": sorted(reasons), "samples": len(sm)}
+
+
+KERNEL_SOURCE = os.path.join(ROOT, "paper_1707_00919_gb300", "csrc", "muca_kernels.cu")
+TRAFFIC_PROFILE = os.path.join(ROOT, "profiles", "sweep_full_kernel_L32_W16384_int8.md")
+
+
+def kernel_source_hash() -> str:
+    import hashlib
+    with open(KERNEL_SOURCE, "rb") as f:
+        return hashlib.sha256(f.read()).hexdigest()[:16]
+
+
+def profiled_traffic():
+    """DRAM bytes (read + write) per recorded-sweep launch from the committed ncu
+    summary, or None when the kernel source changed since that capture."""
+    try:
+        text = open(TRAFFIC_PROFILE).read()
+    except OSError:
+        return None
+    vals = {}
+    for line in text.splitlines():
+        if ":" in line and line.strip().startswith("- "):
+            k, v = line.strip()[2:].split(":", 1)
+            vals[k.strip()] = v.strip().strip("`")
+    if vals.get("kernel_source_sha256_16") != kernel_source_hash():
+        return None
+    try:
+        return float(vals["dram_bytes_per_record_launch"])
+    except (KeyError, ValueError):
+        return None
 
 
 def measured_peaks():
@@ -292,7 +322,7 @@ def run_native(args):
     rec_launch_s = (sum(rec_ms) / len(rec_ms)) / 1e3
     rec_attempts = WALKERS * SWEEPS_PER_ITER * N
     achieved_tops = OPS_PER_ATTEMPT * rec_attempts / rec_launch_s / 1e12
-    traffic = None
+    traffic = profiled_traffic()
     result = {
         "metric": "spin-flip attempts/s (and time-to-flat H) at L=32, 16384 walkers; % of integer-issue roofline",
         "value": value,
@@ -318,7 +348,7 @@ def run_native(args):
         "gpu_launches": 2 * args.steps,
         "roofline": {"bound": "alu", "achieved": achieved_tops, "peak": peak_tops, "unit": "Tops/s (int32)",
                      "frac": achieved_tops / peak_tops, "traffic": traffic,
-                     "kernel": "sweep_kernel<uint32,int8,record>",
+                     "kernel": "sweep_full_kernel<32,int8,record>",
                      "ops_per_attempt": OPS_PER_ATTEMPT,
                      "peak_basis": f"{sm_count} SMs x 4 issue slots x 32 lanes x {sm_max_mhz:.0f} MHz"},
         "clocks": clocks.summary(),
@@ -370,7 +400,7 @@ def run_reference(args):
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--steps", type=int, default=300)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["native", "reference"], default="native")
     ap.add_argument("--no-cpu-baseline", action="store_true")

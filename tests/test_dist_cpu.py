@@ -1,0 +1,72 @@
+"""The method's one exchange step (Sec. 2.2: histograms of independent walkers are
+summed, the new weights are redistributed) across processes: world size 2 with gloo on
+the CPU, each rank advancing its share of the walkers with the oracle.  The all-reduced
+histograms and the weights after every iteration must equal the single-process run
+(walker-keyed random streams make the split invisible)."""
+import os
+import socket
+
+import numpy as np
+import pytest
+
+L, W, SEED, ITERS = 8, 48, 5, 4
+
+
+def _free_port():
+    with socket.socket() as s:
+        s.bind(("127.0.0.1", 0))
+        return s.getsockname()[1]
+
+
+def _rank_main(rank, world, port, out_dir):
+    import sys
+    sys.path.insert(0, os.path.dirname(os.path.dirname(os.path.abspath(__file__))))
+    import torch
+    import torch.distributed as dist
+    from oracle import oracle
+    os.environ["MASTER_ADDR"] = "127.0.0.1"
+    os.environ["MASTER_PORT"] = str(port)
+    dist.init_process_group("gloo", rank=rank, world_size=world)
+    N = L * L
+    share = W // world
+    s, e = oracle.init(L, SEED, share, walker0=rank * share)
+    lnW = np.zeros(N + 1)
+    t = 0
+    hist = []
+    for _ in range(ITERS):
+        T = oracle.build_table(L, lnW)
+        oracle.run(L, SEED, s, e, T, t, 3 * N, False, None, walker0=rank * share)
+        t += 3 * N
+        H = oracle.run(L, SEED, s, e, T, t, 5 * N, True, None, walker0=rank * share)
+        t += 5 * N
+        Ht = torch.from_numpy(H.astype(np.int64))
+        dist.all_reduce(Ht, op=dist.ReduceOp.SUM)
+        H = Ht.numpy().astype(np.uint64)
+        hist.append(H)
+        oracle.update_weights(L, lnW, H)
+    np.save(os.path.join(out_dir, f"lnW_{rank}.npy"), lnW)
+    np.save(os.path.join(out_dir, f"H_{rank}.npy"), np.array(hist))
+    dist.destroy_process_group()
+
+
+def test_sharded_walkers_match_single_process(tmp_path, orc):
+    torch = pytest.importorskip("torch")
+    import torch.multiprocessing as tmp
+    port = _free_port()
+    tmp.spawn(_rank_main, args=(2, port, str(tmp_path)), nprocs=2, join=True)
+    N = L * L
+    s, e = orc.init(L, SEED, W)
+    lnW = np.zeros(N + 1)
+    t = 0
+    ref_hist = []
+    for _ in range(ITERS):
+        T = orc.build_table(L, lnW)
+        orc.run(L, SEED, s, e, T, t, 3 * N, False)
+        t += 3 * N
+        H = orc.run(L, SEED, s, e, T, t, 5 * N, True)
+        t += 5 * N
+        ref_hist.append(H)
+        orc.update_weights(L, lnW, H)
+    for r in range(2):
+        assert np.array_equal(np.load(tmp_path / f"H_{r}.npy"), np.array(ref_hist))
+        assert np.array_equal(np.load(tmp_path / f"lnW_{r}.npy"), lnW)

@@ -278,3 +278,16 @@ def test_paper_schedule_converges_kl(orc):
     # converged weights approximate -ln g up to a constant
     d = (-lnW[acc]) - ex[acc]
     assert np.max(np.abs(d - d.mean())) < 0.15
+
+
+def test_paper_schedule_first_iteration_counts(orc):
+    """Eq. (7) by hand for the first iteration (no range covered yet, so w = 10):
+    N_therm = 30 * 10 = 300 attempts and N_updates = floor(6 * 10^2.25 / 64) + 1 =
+    floor(16.67) + 1 = 17 attempts per walker."""
+    L, W = 8, 64
+    N = L * L
+    s, e = orc.init(L, 2, W)
+    lnW = np.zeros(N + 1)
+    p = orc.make_params(schedule=1, stop_rule=1, flat_threshold=1e-4, max_iterations=1)
+    res, t, _, _ = orc.iterate(L, 2, s, e, lnW, 0, p)
+    assert res.iterations == 1 and t == 300 + 17 and res.attempts == 317
