@@ -85,7 +85,7 @@ constexpr size_t align256(size_t v) { return (v + 255) / 256 * 256; }
 
 // Largest attempts per walker one recorded launch may take so that a block's 32-bit
 // shared histogram bins cannot overflow (each walker adds one count per attempt).
-uint64_t max_recorded_attempts(int wpb) { return 0xFFFFFFFFull / (uint64_t)wpb; }
+uint64_t max_recorded_attempts(int wpb) { return 0xFFFFFFFFull / (uint64_t)std::max(wpb, 256); }
 
 }  // namespace
 
@@ -149,6 +149,8 @@ int check_device_error(muca_t h)
 {
     if (*h->h_err & muca::kErrEnergyRange)
         return fail(MUCA_EDEVICE, "a walker's energy index left the grid [0, N]");
+    if (*h->h_err & muca::kErrSyncTimeout)
+        return fail(MUCA_EDEVICE, "a bounded wait between warps of a sweep kernel timed out");
     if (*h->h_err)
         return fail(MUCA_EDEVICE, "device error word 0x%x", *h->h_err);
     return MUCA_OK;

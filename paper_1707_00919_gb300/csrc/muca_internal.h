@@ -11,6 +11,7 @@ namespace muca {
 
 // Device error word bits.
 constexpr uint32_t kErrEnergyRange = 1u;   // a walker's energy index was off the grid
+constexpr uint32_t kErrSyncTimeout = 2u;   // a bounded wait inside a kernel gave up
 
 struct SweepArgs {
     int32_t L;                  // lattice side (multiple of 4, <= 64)

@@ -540,9 +540,23 @@ __device__ __forceinline__ uint32_t field_x4(uint32_t w, int f)
 
 // One row of L attempts (typewriter, x = 0 .. L-1) for one walker.  E is the shared
 // byte address of the current energy's table row on entry and on exit.
-template <int L, bool RECORD>
+// Random words of the current row: four attempts at a time, already clamped to
+// 0xFFFFFFFE so that "r < T" also accepts every attempt when T = 0xFFFFFFFF.
+struct PhiloxSource {
+    uint64_t blk;            // Philox block of column 0 of the row
+    const PhiloxKeys *pk;
+    __device__ __forceinline__ uint4 get(int xb) const
+    {
+        const uint64_t b = blk + (uint64_t)(xb / 4);
+        const uint4 rw = philox_walker((uint32_t)b, (uint32_t)(b >> 32), *pk);
+        return make_uint4(min(rw.x, 0xFFFFFFFEu), min(rw.y, 0xFFFFFFFEu), min(rw.z, 0xFFFFFFFEu),
+                          min(rw.w, 0xFFFFFFFEu));
+    }
+};
+
+template <int L, bool RECORD, class Src>
 __device__ __forceinline__ void process_row(const uint32_t (&U)[L / 8], uint32_t (&C)[L / 8], const uint32_t (&D)[L / 8],
-                                            uint32_t &E, uint64_t blk, const PhiloxKeys &pk)
+                                            uint32_t &E, const Src &src)
 {
     constexpr int NW = L / 8;
     uint32_t K0[NW], K1[NW];
@@ -584,13 +598,8 @@ __device__ __forceinline__ void process_row(const uint32_t (&U)[L / 8], uint32_t
 
 #pragma unroll
     for (int xb = 0; xb < L; xb += 4) {
-        const uint64_t b = blk + (uint64_t)(xb / 4);
-        const uint4 rw = philox_walker((uint32_t)b, (uint32_t)(b >> 32), pk);
-        uint32_t words[4];
-        words[0] = min(rw.x, 0xFFFFFFFEu);
-        words[1] = min(rw.y, 0xFFFFFFFEu);
-        words[2] = min(rw.z, 0xFFFFFFFEu);
-        words[3] = min(rw.w, 0xFFFFFFFEu);
+        const uint4 rw = src.get(xb);
+        const uint32_t words[4] = {rw.x, rw.y, rw.z, rw.w};
 #pragma unroll
         for (int u = 0; u < 4; ++u) {
             const int x = xb + u;
@@ -699,7 +708,8 @@ __global__ void __launch_bounds__(256, 1) sweep_full_kernel(const SweepArgs a)
         for (uint64_t s = 0; s < nsweeps; ++s) {
 #pragma unroll 1
             for (int y = 0; y < L; ++y) {
-                process_row<L, RECORD>(U, C, D, E, blk, pk);
+                const PhiloxSource src{blk, &pk};
+                process_row<L, RECORD>(U, C, D, E, src);
                 rows.store(y, C);
                 const int y2 = (y + 2 < L) ? y + 2 : y + 2 - L;
 #pragma unroll
