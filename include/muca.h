@@ -66,6 +66,12 @@ extern "C" {
 #define MUCA_LAYOUT_INT8 0       /* int8 spin[site][walker], values +1 / -1                  */
 #define MUCA_LAYOUT_PACKED 1     /* row[y][walker] bit words (bit x set = spin -1);
                                     uint32 words for L <= 32, uint64 for L <= 64          */
+#define MUCA_LAYOUT_AUTO 2       /* muca_create_ex only: time both layouts, keep the faster */
+
+/* walkers_per_block value of muca_create_ex that times every block size from 32 to 256
+ * (two recorded sweeps each on a temporary instance) and keeps the fastest.  0 picks
+ * one from the kernel's occupancy without timing. */
+#define MUCA_WPB_TUNE (-1)
 
 /* Stop rules of the weight iteration. */
 #define MUCA_STOP_MIN_MEAN 0     /* min H / mean H over accessible energies >= threshold    */
@@ -79,13 +85,14 @@ extern "C" {
 typedef struct muca_s *muca_t;
 
 /* Options for muca_create_ex.  Zero-initialise, then set what differs from the
- * defaults (layout MUCA_LAYOUT_INT8, walkers_per_block chosen by the library). */
+ * defaults (layout MUCA_LAYOUT_INT8, walkers_per_block chosen from the occupancy). */
 typedef struct {
     int32_t L;                   /* lattice side: multiple of 4, 4 <= L <= 64               */
     int64_t n_walkers;           /* 1 <= n_walkers <= 2^31 - 1                              */
     uint64_t seed;               /* Philox key                                              */
-    int32_t layout;              /* MUCA_LAYOUT_*                                           */
-    int32_t walkers_per_block;   /* 0 = library default; else a multiple of 32, <= 256      */
+    int32_t layout;              /* MUCA_LAYOUT_* (AUTO: measured choice)                   */
+    int32_t walkers_per_block;   /* 0 = from occupancy, MUCA_WPB_TUNE = measured, else a
+                                    multiple of 32 in [32, 256]                            */
 } muca_options;
 
 /* Parameters of muca_iterate_until_flat.  muca_default_params fills the paper's values
@@ -195,6 +202,40 @@ int muca_synchronize(muca_t h);
  * one key (key[0] low, key[1] high 32 bits of the seed) into out[4*n].  Host buffers;
  * used to check the generator against independent implementations. */
 int muca_philox(const uint32_t *ctr, const uint32_t key[2], size_t n, uint32_t *out);
+
+/* ----------------------------------------------------------------------------------
+ * Batches (Sec. 2.2 applied to many independent simulations at once): one launch of a
+ * persistent kernel advances every member instance; each block takes work items
+ * (instance, 256 or fewer walkers) from a global counter, so instances of uneven L and
+ * walker count share the GPU.  Member instances must have L in {8, 16, 24, 32, 48, 64}.
+ * Results are the same as running each instance alone (walkers and histograms of
+ * different instances never interact).
+ * -------------------------------------------------------------------------------- */
+typedef struct muca_batch_s *muca_batch_t;
+
+/* Groups n existing instances.  The batch does not own them; while it exists their
+ * work runs on the batch's stream (ordered with batch launches); muca_batch_destroy
+ * gives each instance its stream back.  Allocates the launch descriptors, the work list
+ * and the work counters on the device.  Errors: MUCA_EINVAL (NULL, duplicates, L
+ * without a whole-sweep kernel), MUCA_ENOMEM, MUCA_ECUDA. */
+int muca_batch_create(const muca_t *instances, int32_t n, muca_batch_t *out);
+int muca_batch_destroy(muca_batch_t b);
+
+/* Every member performs n_sweeps further sweeps (record as in muca_sweep) in one
+ * batched launch (more if the 32-bit per-block counts require it).  Asynchronous. */
+int muca_batch_sweep(muca_batch_t b, uint64_t n_sweeps, int record);
+
+/* The weight iteration of muca_iterate_until_flat for every member at once (fixed-sweep
+ * schedule only).  Each iteration is one replay of a CUDA graph (table uploads,
+ * thermalization launch, zeroed histograms, recording launch, histogram reads); a member
+ * leaves the work list when its histogram is flat or it reached max_iterations.
+ * stats[i] (may be NULL) receives member i's result, seconds being the wall time until
+ * its last iteration finished.  Returns MUCA_OK if every member became flat, else
+ * MUCA_ENOTCONVERGED or MUCA_ETIMEOUT. */
+int muca_batch_iterate(muca_batch_t b, const muca_params *p, muca_stats *stats);
+
+/* Members, persistent grid size and dynamic shared memory per block of the batch. */
+int muca_batch_info(muca_batch_t b, int32_t *n_instances, int32_t *grid, size_t *smem_bytes);
 
 /* Message of the last failed call on this host thread ("" if none). */
 const char *muca_last_error(void);

@@ -22,6 +22,8 @@ MUCA_EDEVICE = -6
 
 MUCA_LAYOUT_INT8 = 0
 MUCA_LAYOUT_PACKED = 1
+MUCA_LAYOUT_AUTO = 2
+MUCA_WPB_TUNE = -1
 
 MUCA_STOP_MIN_MEAN = 0
 MUCA_STOP_KL = 1
@@ -80,6 +82,11 @@ SIGNATURES = {
     "muca_synchronize": (ctypes.c_int, [_H]),
     "muca_philox": (ctypes.c_int, [_P(ctypes.c_uint32), _P(ctypes.c_uint32), ctypes.c_size_t,
                                    _P(ctypes.c_uint32)]),
+    "muca_batch_create": (ctypes.c_int, [_P(_H), ctypes.c_int32, _P(_H)]),
+    "muca_batch_destroy": (ctypes.c_int, [_H]),
+    "muca_batch_sweep": (ctypes.c_int, [_H, ctypes.c_uint64, ctypes.c_int]),
+    "muca_batch_iterate": (ctypes.c_int, [_H, _P(muca_params), _P(muca_stats)]),
+    "muca_batch_info": (ctypes.c_int, [_H, _P(ctypes.c_int32), _P(ctypes.c_int32), _P(ctypes.c_size_t)]),
     "muca_last_error": (ctypes.c_char_p, []),
 }
 

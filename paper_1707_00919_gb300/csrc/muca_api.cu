@@ -272,6 +272,247 @@ int validate(muca_t h)
     return MUCA_OK;
 }
 
+// Block size for L, layout and W by occupancy: the makespan of a launch is set by the
+// most loaded SM sub-partition (one walker per thread, one warp per 32 walkers), so the
+// cost of a block size is waves x warps per sub-partition in a full wave; ties go to
+// the larger block.
+int default_walkers_per_block(int32_t L, int32_t layout, int64_t W)
+{
+    int dev = 0, sms = 1;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    const size_t limit = muca::sweep_smem_limit();
+    int best = 64;
+    int64_t best_cost = INT64_MAX;
+    for (int wpb = 32; wpb <= 256; wpb += 32) {
+        if (std::max(muca::sweep_smem_bytes(L, wpb, true), muca::full_smem_bytes(L, wpb, true)) > limit)
+            continue;
+        const int occ = muca::resident_blocks(L, layout, wpb);
+        if (occ < 1)
+            continue;
+        const int64_t blocks = (W + wpb - 1) / wpb;
+        const int64_t per_wave = (int64_t)sms * occ;
+        const int64_t waves = (blocks + per_wave - 1) / per_wave;
+        const int64_t first = std::min(blocks, per_wave);
+        const int64_t blocks_per_sm = (first + sms - 1) / sms;
+        const int64_t warps_per_smsp = (blocks_per_sm * (wpb / 32) + 3) / 4;
+        const int64_t cost = waves * warps_per_smsp;
+        if (cost < best_cost || (cost == best_cost && wpb > best)) {
+            best_cost = cost;
+            best = wpb;
+        }
+    }
+    return best;
+}
+
+// Measured choice of layout and/or block size: each candidate runs two recorded sweeps
+// on a temporary instance of the same size; the fastest is kept.
+int tune_options(const muca_options &in, muca_options *out)
+{
+    *out = in;
+    std::vector<int32_t> layouts;
+    if (in.layout == MUCA_LAYOUT_AUTO)
+        layouts = {MUCA_LAYOUT_INT8, MUCA_LAYOUT_PACKED};
+    else
+        layouts = {in.layout};
+    float best_ms = 1e30f;
+    bool found = false;
+    for (int32_t lay : layouts) {
+        std::vector<int32_t> wpbs;
+        if (in.walkers_per_block == MUCA_WPB_TUNE) {
+            for (int wpb = 32; wpb <= 256; wpb += 32)
+                wpbs.push_back(wpb);
+        } else {
+            wpbs.push_back(in.walkers_per_block);
+        }
+        for (int32_t wpb : wpbs) {
+            muca_options o = in;
+            o.layout = lay;
+            o.walkers_per_block = wpb != 0 ? wpb : default_walkers_per_block(in.L, lay, in.n_walkers);
+            if (std::max(muca::sweep_smem_bytes(o.L, o.walkers_per_block, true),
+                         muca::full_smem_bytes(o.L, o.walkers_per_block, true)) > muca::sweep_smem_limit())
+                continue;
+            muca_t t = nullptr;
+            if (muca_create_ex(&o, &t) != MUCA_OK)
+                continue;
+            cudaEvent_t a = nullptr, b = nullptr;
+            float ms = 1e30f;
+            if (cudaEventCreate(&a) == cudaSuccess && cudaEventCreate(&b) == cudaSuccess &&
+                muca_sweep(t, 1, 1) == MUCA_OK && cudaEventRecord(a, t->stream) == cudaSuccess &&
+                muca_sweep(t, 2, 1) == MUCA_OK && cudaEventRecord(b, t->stream) == cudaSuccess &&
+                cudaEventSynchronize(b) == cudaSuccess && cudaEventElapsedTime(&ms, a, b) == cudaSuccess) {
+                if (ms < best_ms) {
+                    best_ms = ms;
+                    *out = o;
+                    found = true;
+                }
+            }
+            if (a)
+                cudaEventDestroy(a);
+            if (b)
+                cudaEventDestroy(b);
+            muca_destroy(t);
+        }
+    }
+    if (!found)
+        return fail(MUCA_EINVAL, "no layout / block size fits L = %d", in.L);
+    return MUCA_OK;
+}
+
+}  // namespace
+
+
+// ---------------------------------------------------------------------------------
+// Batches: many instances advanced by one launch of the batched persistent kernel.
+// ---------------------------------------------------------------------------------
+struct muca_batch_s {
+    std::vector<muca_t> inst;
+    std::vector<cudaStream_t> saved_streams;
+    std::vector<int32_t> item_wpb;        // walkers per work item, per instance
+    Allocator alloc;
+    cudaStream_t stream = nullptr;
+    void *block = nullptr;
+    muca::SweepArgs *d_args = nullptr;    // [2 n]: thermalization launch, recording launch
+    muca::BatchItem *d_items = nullptr;   // capacity: all items of all instances
+    uint32_t *d_counter = nullptr;        // two work counters
+    muca::SweepArgs *h_args = nullptr;    // pinned staging of d_args
+    muca::BatchItem *h_items = nullptr;   // pinned staging of d_items
+    cudaEvent_t staged = nullptr;         // the last upload of h_args / h_items has completed
+    size_t items_capacity = 0;
+    int32_t n_items = 0;                  // items of the current member set
+    std::vector<int32_t> members;         // instances in the current work list
+    size_t smem = 0;
+    int grid = 0;
+    cudaGraphExec_t exec = nullptr;       // one weight iteration of the current members
+    uint64_t g_therm = 0, g_rec = 0;
+};
+
+namespace {
+
+bool batchable_L(int32_t L) { return L == 8 || L == 16 || L == 24 || L == 32 || L == 48 || L == 64; }
+
+// Work items of the given member instances (member index j refers to args[j]),
+// largest first so that the dynamic schedule ends evenly.
+void build_items(muca_batch_t b, const std::vector<int32_t> &members)
+{
+    std::vector<std::pair<int64_t, muca::BatchItem>> v;
+    for (size_t j = 0; j < members.size(); ++j) {
+        const muca_t h = b->inst[(size_t)members[j]];
+        const int32_t wpb = b->item_wpb[(size_t)members[j]];
+        for (int64_t wb = 0; wb < h->W; wb += wpb) {
+            muca::BatchItem it;
+            it.inst = (int32_t)j;
+            it.wpb = wpb;
+            it.wbase = wb;
+            const int64_t cost = (int64_t)h->N * std::min<int64_t>(wpb, h->W - wb);
+            v.emplace_back(cost, it);
+        }
+    }
+    std::stable_sort(v.begin(), v.end(), [](const auto &x, const auto &y) { return x.first > y.first; });
+    b->n_items = (int32_t)v.size();
+    for (size_t i = 0; i < v.size(); ++i)
+        b->h_items[i] = v[i].second;
+    b->members = members;
+}
+
+muca::SweepArgs make_args(muca_t h, uint64_t t0, uint64_t n)
+{
+    muca::SweepArgs a;
+    a.L = h->L;
+    a.layout = h->layout;
+    a.W = h->W;
+    a.seed = h->seed;
+    a.t0 = t0;
+    a.n = n;
+    a.lattice = h->d_lattice;
+    a.energy = h->d_energy;
+    a.table = h->d_table;
+    a.hist = h->d_hist;
+    a.err = h->d_err;
+    return a;
+}
+
+int stage_wait(muca_batch_t b)
+{
+    MUCA_CUDA(cudaEventSynchronize(b->staged), "waiting for the previous batch upload");
+    return MUCA_OK;
+}
+
+int upload_items(muca_batch_t b)
+{
+    MUCA_CUDA(cudaMemcpyAsync(b->d_items, b->h_items, sizeof(muca::BatchItem) * (size_t)b->n_items,
+                              cudaMemcpyHostToDevice, b->stream),
+              "batch work list upload");
+    MUCA_CUDA(cudaEventRecord(b->staged, b->stream), "batch upload event");
+    return MUCA_OK;
+}
+
+int check_members(muca_batch_t b)
+{
+    for (int32_t j : b->members) {
+        int rc = check_device_error(b->inst[(size_t)j]);
+        if (rc)
+            return rc;
+    }
+    return MUCA_OK;
+}
+
+// Captures one weight iteration of the current members: table uploads, the launch
+// descriptors, thermalization launch, zeroed histograms, recording launch, histogram
+// and error-word reads.  The host refills the pinned buffers before every replay.
+int build_graph(muca_batch_t b)
+{
+    if (b->exec) {
+        cudaGraphExecDestroy(b->exec);
+        b->exec = nullptr;
+    }
+    const size_t nm = b->members.size();
+    cudaGraph_t g = nullptr;
+    MUCA_CUDA(cudaStreamBeginCapture(b->stream, cudaStreamCaptureModeThreadLocal), "graph capture begin");
+    cudaError_t err = cudaSuccess;
+    for (int32_t j : b->members) {
+        const muca_t h = b->inst[(size_t)j];
+        if (err == cudaSuccess)
+            err = cudaMemcpyAsync(h->d_table, h->h_table, sizeof(uint32_t) * 5 * ((size_t)h->N + 1),
+                                  cudaMemcpyHostToDevice, b->stream);
+    }
+    if (err == cudaSuccess)
+        err = cudaMemcpyAsync(b->d_args, b->h_args, sizeof(muca::SweepArgs) * 2 * nm, cudaMemcpyHostToDevice,
+                              b->stream);
+    if (err == cudaSuccess)
+        err = cudaMemsetAsync(b->d_counter, 0, 2 * sizeof(uint32_t), b->stream);
+    if (err == cudaSuccess)
+        err = muca::launch_batch(b->d_args, b->d_items, b->n_items, b->d_counter, b->grid, b->smem, false, b->stream);
+    for (int32_t j : b->members) {
+        const muca_t h = b->inst[(size_t)j];
+        if (err == cudaSuccess)
+            err = cudaMemsetAsync(h->d_hist, 0, sizeof(unsigned long long) * ((size_t)h->N + 1), b->stream);
+    }
+    if (err == cudaSuccess)
+        err = muca::launch_batch(b->d_args + nm, b->d_items, b->n_items, b->d_counter + 1, b->grid, b->smem, true,
+                                 b->stream);
+    for (int32_t j : b->members) {
+        const muca_t h = b->inst[(size_t)j];
+        if (err == cudaSuccess)
+            err = cudaMemcpyAsync(h->h_hist, h->d_hist, sizeof(unsigned long long) * ((size_t)h->N + 1),
+                                  cudaMemcpyDeviceToHost, b->stream);
+        if (err == cudaSuccess)
+            err = cudaMemcpyAsync(h->h_err, h->d_err, sizeof(uint32_t), cudaMemcpyDeviceToHost, b->stream);
+    }
+    cudaError_t end = cudaStreamEndCapture(b->stream, &g);
+    if (err == cudaSuccess)
+        err = end;
+    if (err == cudaSuccess)
+        err = cudaGraphInstantiate(&b->exec, g, 0);
+    if (g)
+        cudaGraphDestroy(g);
+    if (err != cudaSuccess) {
+        b->exec = nullptr;
+        return cuda_fail(err, "batch iteration graph");
+    }
+    return MUCA_OK;
+}
+
 }  // namespace
 
 extern "C" {
@@ -327,11 +568,18 @@ int muca_create_ex(const muca_options *opt, muca_t *out)
         return fail(MUCA_EINVAL, "L = %d: must be a multiple of 4 in [4, 64]", L);
     if (opt->n_walkers < 1 || opt->n_walkers > INT32_MAX)
         return fail(MUCA_EINVAL, "n_walkers = %lld out of range", (long long)opt->n_walkers);
-    if (opt->layout != MUCA_LAYOUT_INT8 && opt->layout != MUCA_LAYOUT_PACKED)
+    if (opt->layout != MUCA_LAYOUT_INT8 && opt->layout != MUCA_LAYOUT_PACKED && opt->layout != MUCA_LAYOUT_AUTO)
         return fail(MUCA_EINVAL, "unknown layout %d", opt->layout);
+    if (opt->layout == MUCA_LAYOUT_AUTO || opt->walkers_per_block == MUCA_WPB_TUNE) {
+        muca_options tuned;
+        int rc = tune_options(*opt, &tuned);
+        if (rc != MUCA_OK)
+            return rc;
+        return muca_create_ex(&tuned, out);
+    }
     int32_t wpb = opt->walkers_per_block;
     if (wpb == 0)
-        wpb = 64;
+        wpb = default_walkers_per_block(L, opt->layout, opt->n_walkers);
     if (wpb < 32 || wpb > 256 || wpb % 32 != 0)
         return fail(MUCA_EINVAL, "walkers_per_block = %d: must be a multiple of 32 in [32, 256]", wpb);
     const size_t smem = std::max(muca::sweep_smem_bytes(L, wpb, true), muca::full_smem_bytes(L, wpb, true));
@@ -757,6 +1005,287 @@ int muca_philox(const uint32_t *ctr, const uint32_t key[2], size_t n, uint32_t *
     if (err != cudaSuccess)
         return cuda_fail(err, "philox evaluation");
     return MUCA_OK;
+}
+
+
+int muca_batch_create(const muca_t *instances, int32_t n, muca_batch_t *out)
+{
+    if (!instances || n < 1 || !out)
+        return fail(MUCA_EINVAL, "batch needs at least one instance");
+    *out = nullptr;
+    for (int32_t i = 0; i < n; ++i) {
+        if (!instances[i])
+            return fail(MUCA_EINVAL, "instance %d is NULL", i);
+        if (!batchable_L(instances[i]->L))
+            return fail(MUCA_EINVAL, "instance %d: L = %d has no whole-sweep kernel (8, 16, 24, 32, 48, 64)", i,
+                        instances[i]->L);
+        for (int32_t j = 0; j < i; ++j)
+            if (instances[j] == instances[i])
+                return fail(MUCA_EINVAL, "instance %d appears twice", i);
+    }
+    muca_batch_s *b = new (std::nothrow) muca_batch_s;
+    if (!b)
+        return fail(MUCA_ENOMEM, "host allocation failed");
+    b->inst.assign(instances, instances + n);
+    {
+        std::lock_guard<std::mutex> lock(g_alloc_mutex);
+        b->alloc = g_alloc;
+    }
+    auto cleanup = [&](int rc) {
+        muca_batch_destroy(b);
+        return rc;
+    };
+    const size_t limit = muca::sweep_smem_limit() - 1024;
+    size_t items = 0;
+    for (muca_t h : b->inst) {
+        int32_t wpb = 256;
+        while (wpb > 32 && muca::full_smem_bytes(h->L, wpb, true) > limit)
+            wpb -= 32;
+        b->item_wpb.push_back(wpb);
+        b->smem = std::max(b->smem, muca::full_smem_bytes(h->L, wpb, true));
+        items += (size_t)((h->W + wpb - 1) / wpb);
+    }
+    b->items_capacity = items;
+    cudaError_t err = cudaStreamCreateWithFlags(&b->stream, cudaStreamNonBlocking);
+    if (err == cudaSuccess)
+        err = cudaEventCreateWithFlags(&b->staged, cudaEventDisableTiming);
+    if (err == cudaSuccess)
+        err = muca::configure_batch(b->smem);
+    if (err != cudaSuccess)
+        return cleanup(cuda_fail(err, "batch set-up"));
+    int dev = 0, sms = 1;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    const int occ = muca::batch_resident_blocks(b->smem);
+    if (occ < 1)
+        return cleanup(fail(MUCA_EINVAL, "batched kernel does not fit an SM with %zu bytes of shared memory", b->smem));
+    b->grid = sms * occ;
+    const size_t off_items = align256(sizeof(muca::SweepArgs) * 2 * (size_t)n);
+    const size_t off_counter = off_items + align256(sizeof(muca::BatchItem) * items);
+    b->block = device_alloc(b->alloc, off_counter + 256);
+    if (!b->block)
+        return cleanup(fail(MUCA_ENOMEM, "batch device allocation failed"));
+    b->d_args = static_cast<muca::SweepArgs *>(b->block);
+    b->d_items = reinterpret_cast<muca::BatchItem *>(static_cast<char *>(b->block) + off_items);
+    b->d_counter = reinterpret_cast<uint32_t *>(static_cast<char *>(b->block) + off_counter);
+    err = cudaMallocHost(reinterpret_cast<void **>(&b->h_args), sizeof(muca::SweepArgs) * 2 * (size_t)n);
+    if (err == cudaSuccess)
+        err = cudaMallocHost(reinterpret_cast<void **>(&b->h_items), sizeof(muca::BatchItem) * items);
+    if (err != cudaSuccess)
+        return cleanup(cuda_fail(err, "batch pinned buffers"));
+    // from now on every call on a member instance is ordered with the batch's work
+    for (muca_t h : b->inst) {
+        err = cudaStreamSynchronize(h->stream);
+        if (err != cudaSuccess)
+            return cleanup(cuda_fail(err, "instance synchronize"));
+        b->saved_streams.push_back(h->stream);
+        h->stream = b->stream;
+    }
+    *out = b;
+    return MUCA_OK;
+}
+
+int muca_batch_destroy(muca_batch_t b)
+{
+    if (!b)
+        return MUCA_OK;
+    if (b->stream)
+        cudaStreamSynchronize(b->stream);
+    for (size_t i = 0; i < b->saved_streams.size(); ++i)
+        b->inst[i]->stream = b->saved_streams[i];
+    if (b->exec)
+        cudaGraphExecDestroy(b->exec);
+    device_free(b->alloc, b->block);
+    if (b->h_args)
+        cudaFreeHost(b->h_args);
+    if (b->h_items)
+        cudaFreeHost(b->h_items);
+    if (b->staged)
+        cudaEventDestroy(b->staged);
+    if (b->stream)
+        cudaStreamDestroy(b->stream);
+    delete b;
+    return MUCA_OK;
+}
+
+int muca_batch_info(muca_batch_t b, int32_t *n_instances, int32_t *grid, size_t *smem_bytes)
+{
+    if (!b)
+        return fail(MUCA_EINVAL, "NULL batch");
+    if (n_instances)
+        *n_instances = (int32_t)b->inst.size();
+    if (grid)
+        *grid = b->grid;
+    if (smem_bytes)
+        *smem_bytes = b->smem;
+    return MUCA_OK;
+}
+
+int muca_batch_sweep(muca_batch_t b, uint64_t n_sweeps, int record)
+{
+    if (!b)
+        return fail(MUCA_EINVAL, "NULL batch");
+    if (n_sweeps == 0)
+        return MUCA_OK;
+    for (muca_t h : b->inst)
+        if (h->t % (uint64_t)h->N != 0)
+            return fail(MUCA_EINVAL, "batched launches need every member at a sweep boundary");
+    // every work item is one block: its 32-bit shared counts take 256 walkers x attempts
+    uint64_t max_n = UINT64_MAX;
+    for (muca_t h : b->inst)
+        max_n = std::min<uint64_t>(max_n, (record ? 0xFFFFFFFFull / 256ull : UINT64_MAX) / (uint64_t)h->N);
+    std::vector<int32_t> all(b->inst.size());
+    for (size_t i = 0; i < all.size(); ++i)
+        all[i] = (int32_t)i;
+    int rc = stage_wait(b);
+    if (rc)
+        return rc;
+    if (b->members != all) {
+        build_items(b, all);
+        if (b->exec) {
+            cudaGraphExecDestroy(b->exec);
+            b->exec = nullptr;
+        }
+    }
+    rc = upload_items(b);
+    if (rc)
+        return rc;
+    while (n_sweeps > 0) {
+        const uint64_t chunk = std::min(n_sweeps, max_n);
+        rc = stage_wait(b);
+        if (rc)
+            return rc;
+        for (size_t j = 0; j < b->inst.size(); ++j) {
+            muca_t h = b->inst[j];
+            b->h_args[j] = make_args(h, h->t, chunk * (uint64_t)h->N);
+            h->t += chunk * (uint64_t)h->N;
+        }
+        MUCA_CUDA(cudaMemcpyAsync(b->d_args, b->h_args, sizeof(muca::SweepArgs) * b->inst.size(),
+                                  cudaMemcpyHostToDevice, b->stream),
+                  "batch descriptor upload");
+        MUCA_CUDA(cudaEventRecord(b->staged, b->stream), "batch upload event");
+        MUCA_CUDA(cudaMemsetAsync(b->d_counter, 0, sizeof(uint32_t), b->stream), "work counter reset");
+        MUCA_CUDA(muca::launch_batch(b->d_args, b->d_items, b->n_items, b->d_counter, b->grid, b->smem, record != 0,
+                                     b->stream),
+                  "batched launch");
+        n_sweeps -= chunk;
+    }
+    return MUCA_OK;
+}
+
+int muca_batch_iterate(muca_batch_t b, const muca_params *p_in, muca_stats *stats)
+{
+    if (!b)
+        return fail(MUCA_EINVAL, "NULL batch");
+    muca_params p;
+    if (p_in)
+        p = *p_in;
+    else
+        muca_default_params(&p);
+    if (p.schedule != MUCA_SCHEDULE_SWEEPS)
+        return fail(MUCA_EINVAL, "batched iteration supports the fixed-sweep schedule");
+    if (p.stop_rule < MUCA_STOP_MIN_MEAN || p.stop_rule > MUCA_STOP_CHEBYSHEV || p.max_iterations < 1)
+        return fail(MUCA_EINVAL, "bad stop rule or max_iterations");
+    for (muca_t h : b->inst) {
+        if ((p.sweeps_per_iter * (uint64_t)h->N) > 0xFFFFFFFFull / 256ull)
+            return fail(MUCA_EINVAL, "sweeps_per_iter too large for one recording launch");
+        if (h->t % (uint64_t)h->N != 0)
+            return fail(MUCA_EINVAL, "batched launches need every member at a sweep boundary");
+    }
+    const auto start = std::chrono::steady_clock::now();
+    const size_t n = b->inst.size();
+    std::vector<muca_stats> st(n);
+    std::memset(st.data(), 0, sizeof(muca_stats) * n);
+    std::vector<int32_t> active(n);
+    for (size_t i = 0; i < n; ++i)
+        active[i] = (int32_t)i;
+    int rc = stage_wait(b);
+    if (rc)
+        return rc;
+    MUCA_CUDA(cudaStreamSynchronize(b->stream), "batch synchronize");
+    bool timed_out = false;
+    std::vector<uint64_t> H;
+    while (!active.empty()) {
+        if (active != b->members || !b->exec || b->g_therm != p.therm_sweeps || b->g_rec != p.sweeps_per_iter) {
+            build_items(b, active);
+            rc = upload_items(b);
+            if (rc)
+                return rc;
+            MUCA_CUDA(cudaStreamSynchronize(b->stream), "batch synchronize");
+            rc = build_graph(b);
+            if (rc)
+                return rc;
+            b->g_therm = p.therm_sweeps;
+            b->g_rec = p.sweeps_per_iter;
+        }
+        const size_t nm = active.size();
+        for (size_t j = 0; j < nm; ++j) {
+            muca_t h = b->inst[(size_t)active[j]];
+            build_table(h->L, h->lnW, h->h_table);
+            const uint64_t nt = p.therm_sweeps * (uint64_t)h->N, nr = p.sweeps_per_iter * (uint64_t)h->N;
+            b->h_args[j] = make_args(h, h->t, nt);
+            b->h_args[nm + j] = make_args(h, h->t + nt, nr);
+            h->t += nt + nr;
+        }
+        MUCA_CUDA(cudaGraphLaunch(b->exec, b->stream), "batch iteration launch");
+        MUCA_CUDA(cudaStreamSynchronize(b->stream), "batch synchronize");
+        rc = check_members(b);
+        if (rc)
+            return rc;
+        const double now = std::chrono::duration<double>(std::chrono::steady_clock::now() - start).count();
+        std::vector<int32_t> next;
+        for (size_t j = 0; j < nm; ++j) {
+            const int32_t i = active[j];
+            muca_t h = b->inst[(size_t)i];
+            const int32_t N = h->N;
+            H.assign(h->h_hist, h->h_hist + N + 1);
+            muca_stats &s = st[(size_t)i];
+            s.iterations += 1;
+            s.attempts_per_walker += (p.therm_sweeps + p.sweeps_per_iter) * (uint64_t)N;
+            double metric;
+            if (p.stop_rule == MUCA_STOP_MIN_MEAN)
+                metric = min_over_mean(N, H);
+            else if (p.stop_rule == MUCA_STOP_KL)
+                metric = kullback_leibler(N, H, (double)(N - 1));
+            else
+                metric = chebyshev(N, H);
+            s.last_metric = metric;
+            s.seconds = now;
+            const bool flat = p.stop_rule == MUCA_STOP_MIN_MEAN ? metric >= p.flat_threshold : metric < p.flat_threshold;
+            if (flat) {
+                s.converged = 1;
+                continue;
+            }
+            for (int32_t e = 0; e <= N; ++e)
+                if (H[(size_t)e])
+                    h->lnW[(size_t)e] -= std::log((double)H[(size_t)e]);
+            if (s.iterations < p.max_iterations)
+                next.push_back(i);
+        }
+        active.swap(next);
+        if (p.deadline_s > 0.0 && now > p.deadline_s && !active.empty()) {
+            timed_out = true;
+            break;
+        }
+    }
+    // device tables follow the host weights again
+    for (muca_t h : b->inst) {
+        rc = upload_table(h);
+        if (rc)
+            return rc;
+    }
+    MUCA_CUDA(cudaStreamSynchronize(b->stream), "batch synchronize");
+    bool all = true;
+    for (size_t i = 0; i < n; ++i) {
+        all = all && st[i].converged;
+        if (stats)
+            stats[i] = st[i];
+    }
+    if (all)
+        return MUCA_OK;
+    if (timed_out)
+        return fail(MUCA_ETIMEOUT, "deadline of %.3f s passed", p.deadline_s);
+    return fail(MUCA_ENOTCONVERGED, "not every instance became flat");
 }
 
 const char *muca_last_error(void) { return g_last_error.c_str(); }

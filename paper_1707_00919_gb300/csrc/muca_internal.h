@@ -27,6 +27,15 @@ struct SweepArgs {
     uint32_t *err;              // device error word
 };
 
+// One work item of the batched kernel: walkers wbase .. wbase + wpb - 1 of instance inst.
+struct BatchItem {
+    int32_t inst;
+    int32_t wpb;
+    int64_t wbase;
+};
+
+constexpr int kBatchThreads = 256;   // threads per block of the batched kernel
+
 // Shared memory bytes a sweep launch with this many walkers per block needs.
 size_t sweep_smem_bytes(int L, int walkers_per_block, bool record);
 
@@ -56,6 +65,19 @@ cudaError_t launch_unpack(int32_t L, int32_t layout, int64_t W, const void *latt
 // Evaluates the device Philox4x32-10 on n counters.
 cudaError_t launch_philox(const uint32_t *ctr, uint32_t k0, uint32_t k1, size_t n, uint32_t *out,
                           cudaStream_t s);
+
+// Blocks of the recording sweep kernel for this L, layout and block size that one SM
+// holds at once (0 if the configuration does not fit).
+int resident_blocks(int L, int layout, int walkers_per_block);
+
+// Batched persistent kernel: allows `smem` bytes of dynamic shared memory, reports how
+// many blocks of it an SM holds, and launches it over a work list (counter zeroed by
+// the caller before every launch; L must be one of 8, 16, 24, 32, 48, 64 and every
+// launch covers whole sweeps).
+cudaError_t configure_batch(size_t smem);
+int batch_resident_blocks(size_t smem);
+cudaError_t launch_batch(const SweepArgs *insts, const BatchItem *items, int32_t n_items, uint32_t *counter,
+                         int grid, size_t smem, bool record, cudaStream_t s);
 
 // Bytes of the lattice storage of W walkers.
 size_t lattice_bytes(int32_t L, int32_t layout, int64_t W);

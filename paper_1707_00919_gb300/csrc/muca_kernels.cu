@@ -640,26 +640,29 @@ __device__ __forceinline__ void process_row(const uint32_t (&U)[L / 8], uint32_t
     E = Eres;
 }
 
+// One block's share of a launch: walkers wbase .. wbase + wpb - 1 of the instance in
+// `a` (threads tid >= wpb idle), all of the launch's whole sweeps.  Shared memory:
+// the table, then the rows of the wpb walkers.  Every thread of the block calls it.
 template <int L, int LAYOUT, bool RECORD>
-__global__ void __launch_bounds__(256, 1) sweep_full_kernel(const SweepArgs a)
+__device__ __forceinline__ void sweep_block(const SweepArgs &a, int64_t wbase, int wpb, unsigned char *smem)
 {
     using RowT = typename RowOf<L>::type;
     constexpr int N = L * L;
     constexpr int NB = N + 1;
     constexpr int NW = L / 8;
     constexpr int RB = 4;   // rows per batch of int8 loads
-    extern __shared__ __align__(16) unsigned char smem[];
-    const int wpb = blockDim.x;
+    const int nthr = blockDim.x;
     uint32_t *sTab = reinterpret_cast<uint32_t *>(smem);
     const int tid = threadIdx.x;
     const SmemRows<L> rows{smem + align_up((size_t)NB * kTableStride * 4, 16), wpb, tid};
     const int lane = tid & 31;
-    const int64_t w = (int64_t)blockIdx.x * wpb + tid;
+    const bool in_item = tid < wpb;
+    const int64_t w = wbase + tid;
     const int64_t w0 = w - lane;
-    bool active = w < a.W;
-    const bool warp_full = (w0 + 32 <= a.W) && (a.W % 16 == 0);
+    bool active = in_item && w < a.W;
+    const bool warp_full = in_item && (w0 + 32 <= a.W) && (a.W % 16 == 0);
 
-    for (int i = tid; i < NB * kTableStride; i += wpb) {
+    for (int i = tid; i < NB * kTableStride; i += nthr) {
         const int e = i / kTableStride, k = i - e * kTableStride;
         sTab[i] = k < 5 ? a.table[e * 5 + k] : 0u;
     }
@@ -725,7 +728,7 @@ __global__ void __launch_bounds__(256, 1) sweep_full_kernel(const SweepArgs a)
     }
     __syncthreads();
     if (RECORD)
-        for (int i = tid; i < NB; i += wpb) {
+        for (int i = tid; i < NB; i += nthr) {
             const uint32_t v = sTab[i * kTableStride + kHistSlot];
             if (v)
                 atomicAdd(&a.hist[i], (unsigned long long)v);
@@ -748,6 +751,58 @@ __global__ void __launch_bounds__(256, 1) sweep_full_kernel(const SweepArgs a)
     }
     if (active)
         a.energy[w] = e;
+}
+
+template <int L, int LAYOUT, bool RECORD>
+__global__ void __launch_bounds__(256, 1) sweep_full_kernel(const SweepArgs a)
+{
+    extern __shared__ __align__(16) unsigned char smem[];
+    sweep_block<L, LAYOUT, RECORD>(a, (int64_t)blockIdx.x * blockDim.x, blockDim.x, smem);
+}
+
+// ---------------------------------------------------------------------------------
+// Batched persistent kernel: one launch advances many instances (uneven L, walker
+// counts, tables and histograms).  The work list holds (instance, first walker, walker
+// count) items; each block takes the next item from a global counter, runs it with the
+// body of the whole-sweep kernel for that instance's L and layout, and takes another
+// until the list is exhausted.  The counter must be zero at launch.
+// ---------------------------------------------------------------------------------
+template <int L, bool RECORD>
+__device__ __forceinline__ void batch_item(const SweepArgs &a, const BatchItem &it, unsigned char *smem)
+{
+    if (a.layout == MUCA_LAYOUT_PACKED)
+        sweep_block<L, MUCA_LAYOUT_PACKED, RECORD>(a, it.wbase, it.wpb, smem);
+    else
+        sweep_block<L, MUCA_LAYOUT_INT8, RECORD>(a, it.wbase, it.wpb, smem);
+}
+
+template <bool RECORD>
+__global__ void __launch_bounds__(256, 1) batch_kernel(const SweepArgs *__restrict__ insts,
+                                                        const BatchItem *__restrict__ items, int32_t n_items,
+                                                        uint32_t *counter)
+{
+    extern __shared__ __align__(16) unsigned char smem[];
+    __shared__ int32_t s_item;
+    for (;;) {
+        if (threadIdx.x == 0)
+            s_item = (int32_t)atomicAdd(counter, 1u);
+        __syncthreads();
+        const int32_t k = s_item;
+        __syncthreads();
+        if (k >= n_items)
+            break;
+        const BatchItem it = items[k];
+        const SweepArgs a = insts[it.inst];
+        switch (a.L) {
+        case 8: batch_item<8, RECORD>(a, it, smem); break;
+        case 16: batch_item<16, RECORD>(a, it, smem); break;
+        case 24: batch_item<24, RECORD>(a, it, smem); break;
+        case 32: batch_item<32, RECORD>(a, it, smem); break;
+        case 48: batch_item<48, RECORD>(a, it, smem); break;
+        case 64: batch_item<64, RECORD>(a, it, smem); break;
+        default: break;
+        }
+    }
 }
 
 template <int L, int LAYOUT, bool RECORD>
@@ -790,6 +845,30 @@ cudaError_t launch_full(const SweepArgs &a, int wpb, bool record, cudaStream_t s
     case 64: return launch_full_l<64>(a, wpb, record, s);
     default: return cudaErrorNotSupported;
     }
+}
+
+template <int L, int LAYOUT>
+int occupancy_full_t(int wpb)
+{
+    const size_t smem = full_smem_bytes(L, wpb, true);
+    auto kern = sweep_full_kernel<L, LAYOUT, true>;
+    if (smem > 48 * 1024 && cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess) {
+        cudaGetLastError();
+        return 0;
+    }
+    int n = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, kern, wpb, smem) != cudaSuccess) {
+        cudaGetLastError();
+        return 0;
+    }
+    return n;
+}
+
+template <int L>
+int occupancy_full_l(int layout, int wpb)
+{
+    return layout == MUCA_LAYOUT_PACKED ? occupancy_full_t<L, MUCA_LAYOUT_PACKED>(wpb)
+                                        : occupancy_full_t<L, MUCA_LAYOUT_INT8>(wpb);
 }
 
 bool has_full_kernel(int L) { return L == 8 || L == 16 || L == 24 || L == 32 || L == 48 || L == 64; }
@@ -927,6 +1006,58 @@ cudaError_t launch_philox(const uint32_t *ctr, uint32_t k0, uint32_t k1, size_t 
         return cudaSuccess;
     const int threads = 128;
     philox_kernel<<<(unsigned)((n + threads - 1) / threads), threads, 0, s>>>(ctr, k0, k1, n, out);
+    return cudaGetLastError();
+}
+
+int resident_blocks(int L, int layout, int wpb)
+{
+    switch (L) {
+    case 8: return occupancy_full_l<8>(layout, wpb);
+    case 16: return occupancy_full_l<16>(layout, wpb);
+    case 24: return occupancy_full_l<24>(layout, wpb);
+    case 32: return occupancy_full_l<32>(layout, wpb);
+    case 48: return occupancy_full_l<48>(layout, wpb);
+    case 64: return occupancy_full_l<64>(layout, wpb);
+    default: break;
+    }
+    // the generic kernel: bounded by shared memory and threads
+    int dev = 0, smem_sm = 0, thr_sm = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&smem_sm, cudaDevAttrMaxSharedMemoryPerMultiprocessor, dev);
+    cudaDeviceGetAttribute(&thr_sm, cudaDevAttrMaxThreadsPerMultiProcessor, dev);
+    const size_t need = sweep_smem_bytes(L, wpb, true) + 1024;
+    return (int)std::min((size_t)smem_sm / need, (size_t)(thr_sm / wpb));
+}
+
+cudaError_t configure_batch(size_t smem)
+{
+    for (auto kern : {batch_kernel<true>, batch_kernel<false>}) {
+        cudaError_t err = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (err != cudaSuccess)
+            return err;
+    }
+    return cudaSuccess;
+}
+
+int batch_resident_blocks(size_t smem)
+{
+    int n = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, batch_kernel<true>, kBatchThreads, smem) != cudaSuccess) {
+        cudaGetLastError();
+        return 0;
+    }
+    return n;
+}
+
+cudaError_t launch_batch(const SweepArgs *insts, const BatchItem *items, int32_t n_items, uint32_t *counter,
+                         int grid, size_t smem, bool record, cudaStream_t s)
+{
+    if (n_items <= 0)
+        return cudaSuccess;
+    if (record)
+        batch_kernel<true><<<grid, kBatchThreads, smem, s>>>(insts, items, n_items, counter);
+    else
+        batch_kernel<false><<<grid, kBatchThreads, smem, s>>>(insts, items, n_items, counter);
     return cudaGetLastError();
 }
 

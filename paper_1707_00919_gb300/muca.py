@@ -13,7 +13,8 @@ from dataclasses import dataclass
 import numpy as np
 
 from . import _lib as C
-from ._lib import (MUCA_LAYOUT_INT8, MUCA_LAYOUT_PACKED, MUCA_OK, MUCA_SCHEDULE_PAPER,  # noqa: F401
+from ._lib import (MUCA_LAYOUT_AUTO, MUCA_LAYOUT_INT8, MUCA_LAYOUT_PACKED, MUCA_OK,  # noqa: F401
+                   MUCA_SCHEDULE_PAPER, MUCA_WPB_TUNE,
                    MUCA_SCHEDULE_SWEEPS, MUCA_STOP_CHEBYSHEV, MUCA_STOP_KL, MUCA_STOP_MIN_MEAN,
                    muca_options, muca_params, muca_stats)
 
@@ -285,3 +286,71 @@ class Muca:
 
     def synchronize(self) -> None:
         muca_synchronize(self._h)
+
+
+# ---------------------------------------------------------------------------------
+# batches
+# ---------------------------------------------------------------------------------
+def muca_batch_create(handles) -> ctypes.c_void_p:
+    arr = (ctypes.c_void_p * len(handles))(*[h.value if isinstance(h, ctypes.c_void_p) else h for h in handles])
+    b = ctypes.c_void_p()
+    _check(C.load().muca_batch_create(arr, len(handles), ctypes.byref(b)))
+    return b
+
+
+def muca_batch_destroy(b) -> None:
+    _check(C.load().muca_batch_destroy(b))
+
+
+def muca_batch_sweep(b, n_sweeps: int, record: bool) -> None:
+    _check(C.load().muca_batch_sweep(b, n_sweeps, 1 if record else 0))
+
+
+def muca_batch_iterate(b, n: int, params: muca_params | None = None, raise_on_fail: bool = False):
+    st = (muca_stats * n)()
+    rc = C.load().muca_batch_iterate(b, ctypes.byref(params) if params is not None else None, st)
+    if raise_on_fail:
+        _check(rc)
+    return rc, [IterationStats(rc, s.iterations, bool(s.converged), s.last_metric, s.attempts_per_walker, s.seconds)
+                for s in st]
+
+
+def muca_batch_info(b):
+    n, g, sm = ctypes.c_int32(), ctypes.c_int32(), ctypes.c_size_t()
+    _check(C.load().muca_batch_info(b, ctypes.byref(n), ctypes.byref(g), ctypes.byref(sm)))
+    return n.value, g.value, sm.value
+
+
+class Batch:
+    """Several Muca instances advanced together by the batched persistent kernel."""
+
+    def __init__(self, instances):
+        self.instances = list(instances)
+        self._b = muca_batch_create([m._h for m in self.instances])
+
+    def sweep(self, n_sweeps: int, record: bool = True) -> None:
+        muca_batch_sweep(self._b, n_sweeps, record)
+
+    def iterate_until_flat(self, params: muca_params | None = None):
+        rc, stats = muca_batch_iterate(self._b, len(self.instances), params)
+        return rc, stats
+
+    def info(self):
+        return muca_batch_info(self._b)
+
+    def close(self) -> None:
+        if self._b:
+            muca_batch_destroy(self._b)
+            self._b = None
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

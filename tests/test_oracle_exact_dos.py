@@ -78,3 +78,19 @@ def test_fixture_matches_generator(orc, L):
     g = orc.dos_bruteforce(L) if L == 4 else (orc.dos_transfer(L) if L <= 8 else load_exact_dos_integers(L))
     ref = np.array([math.log(x) if x else -np.inf for x in g])
     assert np.array_equal(lg, ref)
+
+
+def test_fixture_L64_log_values():
+    lg = load_exact_ln_dos(64)
+    N = 4096
+    assert lg.shape == (N + 1,)
+    fin = np.isfinite(lg)
+    assert [e for e in range(N + 1) if not fin[e]] == [1, N - 1]
+    m = lg[fin].max()
+    total = m + math.log(np.exp(lg[fin] - m).sum())
+    assert abs(total - N * math.log(2.0)) < 1e-9 * N
+    assert lg[0] == pytest.approx(math.log(2))
+    assert lg[2] == pytest.approx(math.log(2 * N))
+    assert lg[3] == pytest.approx(math.log(4 * N))
+    assert lg[4] == pytest.approx(math.log(N * (N - 1) + 10 * N))
+    assert np.allclose(lg[fin], lg[::-1][fin], rtol=0, atol=1e-12)
