@@ -237,6 +237,55 @@ int muca_batch_iterate(muca_batch_t b, const muca_params *p, muca_stats *stats);
 /* Members, persistent grid size and dynamic shared memory per block of the batch. */
 int muca_batch_info(muca_batch_t b, int32_t *n_instances, int32_t *grid, size_t *smem_bytes);
 
+/* ----------------------------------------------------------------------------------
+ * Allocation-free batched sweep.  The paper has no counterpart: this entry point exists
+ * for callers that must not allocate device memory while they run, for instance an
+ * application that owns the GPU's memory and lends out fixed buffers reserved at start-up,
+ * a plugin whose host forbids allocation after initialisation, or a loop that cannot
+ * afford the device-wide synchronisation a cudaMalloc/cudaFree may cause.  Such a caller
+ * passes its own device buffers; the call allocates nothing (no cudaMalloc, cudaFree or
+ * allocating library routine).  The kernel's scratch (instance descriptors, work-list
+ * bookkeeping and the work counter, MUCA_NOALLOC_SCRATCH_BYTES in total) is a fixed array
+ * in device memory that every GPU loading this library keeps until the process exits.
+ * -------------------------------------------------------------------------------- */
+#define MUCA_NOALLOC_MAX_INSTANCES 64
+#define MUCA_NOALLOC_SCRATCH_BYTES 8192
+
+/* One instance's state in caller-owned device memory, in the layouts of this header:
+ * lattice in `layout`, energy indices int32[n_walkers], thresholds uint32[(L*L+1)*5]
+ * (as muca_get_table returns them), histogram uint64[L*L+1] (added to), error word
+ * uint32 (bits OR-ed in, 0 = fine).  t0 is the attempt counter of the first attempt and
+ * must lie on a sweep boundary (a multiple of L*L). */
+typedef struct {
+    int32_t L;                   /* one of 8, 16, 24, 32, 48, 64                           */
+    int32_t layout;              /* MUCA_LAYOUT_INT8 or MUCA_LAYOUT_PACKED                 */
+    int64_t n_walkers;
+    uint64_t seed;
+    uint64_t t0;
+    void *lattice;
+    int32_t *energy;
+    const uint32_t *table;
+    unsigned long long *hist;
+    uint32_t *err;
+} muca_raw_instance;
+
+/* Every one of the n instances (at most MUCA_NOALLOC_MAX_INSTANCES) performs n_sweeps
+ * whole sweeps (record as in muca_sweep) in one launch of the batched kernel on
+ * cuda_stream (NULL = the default stream); results are those of muca_batch_sweep on the
+ * same state.  The caller advances its t0 by n_sweeps * L * L afterwards.
+ *  - The first call on a device looks up the scratch array's device address (once per
+ *    device, with that device current); make that first call before any stream capture.
+ *  - The instance table is copied from the caller's host array, so the array may be
+ *    reused as soon as the call returns.
+ *  - All calls share the one scratch array, which keeps the last call's contents: calls
+ *    that overlap on the GPU (other streams, other host threads) race and must not be
+ *    issued.
+ * Errors: MUCA_EINVAL (NULL, more than MUCA_NOALLOC_MAX_INSTANCES instances, L outside
+ * the list, t0 off a sweep boundary, a recorded launch longer than 0xFFFFFFFF / 256
+ * attempts per walker), MUCA_ECUDA. */
+int muca_batch_sweep_noalloc(const muca_raw_instance *instances, int32_t n, uint64_t n_sweeps, int record,
+                             void *cuda_stream);
+
 /* Message of the last failed call on this host thread ("" if none). */
 const char *muca_last_error(void);
 

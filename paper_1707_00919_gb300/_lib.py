@@ -52,6 +52,16 @@ class muca_stats(ctypes.Structure):
                 ("seconds", ctypes.c_double)]
 
 
+class muca_raw_instance(ctypes.Structure):
+    _fields_ = [("L", ctypes.c_int32), ("layout", ctypes.c_int32), ("n_walkers", ctypes.c_int64),
+                ("seed", ctypes.c_uint64), ("t0", ctypes.c_uint64), ("lattice", ctypes.c_void_p),
+                ("energy", ctypes.c_void_p), ("table", ctypes.c_void_p), ("hist", ctypes.c_void_p),
+                ("err", ctypes.c_void_p)]
+
+
+MUCA_NOALLOC_MAX_INSTANCES = 64
+MUCA_NOALLOC_SCRATCH_BYTES = 8192
+
 ALLOC_FN = ctypes.CFUNCTYPE(ctypes.c_void_p, ctypes.c_size_t, ctypes.c_void_p)
 RELEASE_FN = ctypes.CFUNCTYPE(None, ctypes.c_void_p, ctypes.c_void_p)
 
@@ -87,6 +97,8 @@ SIGNATURES = {
     "muca_batch_sweep": (ctypes.c_int, [_H, ctypes.c_uint64, ctypes.c_int]),
     "muca_batch_iterate": (ctypes.c_int, [_H, _P(muca_params), _P(muca_stats)]),
     "muca_batch_info": (ctypes.c_int, [_H, _P(ctypes.c_int32), _P(ctypes.c_int32), _P(ctypes.c_size_t)]),
+    "muca_batch_sweep_noalloc": (ctypes.c_int, [_P(muca_raw_instance), ctypes.c_int32, ctypes.c_uint64, ctypes.c_int,
+                                                ctypes.c_void_p]),
     "muca_last_error": (ctypes.c_char_p, []),
 }
 

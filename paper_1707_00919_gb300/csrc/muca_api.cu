@@ -1288,6 +1288,59 @@ int muca_batch_iterate(muca_batch_t b, const muca_params *p_in, muca_stats *stat
     return fail(MUCA_ENOTCONVERGED, "not every instance became flat");
 }
 
+
+int muca_batch_sweep_noalloc(const muca_raw_instance *instances, int32_t n, uint64_t n_sweeps, int record,
+                             void *cuda_stream)
+{
+    if (!instances || n < 1)
+        return fail(MUCA_EINVAL, "no instances given");
+    if (n > MUCA_NOALLOC_MAX_INSTANCES)
+        return fail(MUCA_EINVAL, "%d instances exceed the allocation-free limit of %d", n, MUCA_NOALLOC_MAX_INSTANCES);
+    if (n_sweeps == 0)
+        return MUCA_OK;
+    const size_t limit = muca::sweep_smem_limit() - 1024;
+    muca::SweepArgs descs[MUCA_NOALLOC_MAX_INSTANCES];
+    int32_t wpbs[MUCA_NOALLOC_MAX_INSTANCES];
+    size_t smem = 0;
+    for (int32_t i = 0; i < n; ++i) {
+        const muca_raw_instance &r = instances[i];
+        if (!batchable_L(r.L))
+            return fail(MUCA_EINVAL, "instance %d: L = %d not in {8, 16, 24, 32, 48, 64}", i, r.L);
+        if (r.layout != MUCA_LAYOUT_INT8 && r.layout != MUCA_LAYOUT_PACKED)
+            return fail(MUCA_EINVAL, "instance %d: unknown layout %d", i, r.layout);
+        if (r.n_walkers < 1 || r.n_walkers > INT32_MAX)
+            return fail(MUCA_EINVAL, "instance %d: n_walkers = %lld out of range", i, (long long)r.n_walkers);
+        if (!r.lattice || !r.energy || !r.table || !r.hist || !r.err)
+            return fail(MUCA_EINVAL, "instance %d: NULL device buffer", i);
+        const uint64_t N = (uint64_t)r.L * (uint64_t)r.L;
+        if (r.t0 % N != 0)
+            return fail(MUCA_EINVAL, "instance %d: t0 is not at a sweep boundary", i);
+        if (n_sweeps > UINT64_MAX / N || (record && n_sweeps * N > 0xFFFFFFFFull / 256ull))
+            return fail(MUCA_EINVAL, "instance %d: %llu sweeps exceed one launch (at most %llu recorded attempts per walker)",
+                        i, (unsigned long long)n_sweeps, (unsigned long long)(0xFFFFFFFFull / 256ull));
+        int32_t wpb = 256;
+        while (wpb > 32 && muca::full_smem_bytes(r.L, wpb, true) > limit)
+            wpb -= 32;
+        wpbs[i] = wpb;
+        smem = std::max(smem, muca::full_smem_bytes(r.L, wpb, true));
+        muca::SweepArgs &d = descs[i];
+        d.L = r.L;
+        d.layout = r.layout;
+        d.W = r.n_walkers;
+        d.seed = r.seed;
+        d.t0 = r.t0;
+        d.n = n_sweeps * N;
+        d.lattice = r.lattice;
+        d.energy = r.energy;
+        d.table = r.table;
+        d.hist = r.hist;
+        d.err = r.err;
+    }
+    MUCA_CUDA(muca::launch_batch_noalloc(descs, wpbs, n, smem, record != 0, static_cast<cudaStream_t>(cuda_stream)),
+              "allocation-free batched sweep");
+    return MUCA_OK;
+}
+
 const char *muca_last_error(void) { return g_last_error.c_str(); }
 
 }  // extern "C"

@@ -79,6 +79,18 @@ int batch_resident_blocks(size_t smem);
 cudaError_t launch_batch(const SweepArgs *insts, const BatchItem *items, int32_t n_items, uint32_t *counter,
                          int grid, size_t smem, bool record, cudaStream_t s);
 
+// Allocation-free batched sweep (see muca_batch_sweep_noalloc in muca.h): descriptors
+// and walkers per item come from the host; the kernel's scratch is a file-scope device
+// array of kNoAllocScratchBytes, looked up on the first call per device.
+constexpr int kNoAllocMaxInstances = 64;
+constexpr int kNoAllocMaxDevices = 64;
+constexpr size_t kNoAllocWpbOffset = sizeof(SweepArgs) * kNoAllocMaxInstances;
+constexpr size_t kNoAllocCounterOffset = kNoAllocWpbOffset + sizeof(int32_t) * (2 * kNoAllocMaxInstances + 1);
+constexpr size_t kNoAllocScratchBytes = 8192;
+static_assert(kNoAllocCounterOffset + sizeof(uint32_t) <= kNoAllocScratchBytes, "scratch layout");
+cudaError_t launch_batch_noalloc(const SweepArgs *descs, const int32_t *wpbs, int32_t n, size_t smem, bool record,
+                                 cudaStream_t s);
+
 // Bytes of the lattice storage of W walkers.
 size_t lattice_bytes(int32_t L, int32_t layout, int64_t W);
 

@@ -354,3 +354,10 @@ class Batch:
             self.close()
         except Exception:
             pass
+
+
+def muca_batch_sweep_noalloc(instances, n_sweeps: int, record: bool, stream_handle: int | None = None) -> None:
+    """instances: muca_raw_instance structures (caller-owned device buffers)."""
+    arr = (C.muca_raw_instance * len(instances))(*instances)
+    _check(C.load().muca_batch_sweep_noalloc(arr, len(instances), n_sweeps, 1 if record else 0,
+                                             ctypes.c_void_p(stream_handle or 0)))
