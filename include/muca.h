@@ -238,6 +238,58 @@ int muca_batch_iterate(muca_batch_t b, const muca_params *p, muca_stats *stats);
 int muca_batch_info(muca_batch_t b, int32_t *n_instances, int32_t *grid, size_t *smem_bytes);
 
 /* ----------------------------------------------------------------------------------
+ * Serving: weight iterations requested over time.  A request is admitted (its instance
+ * created and kept resident on the device) as soon as its device memory fits the
+ * server's budget; every muca_server_step advances all admitted requests by one
+ * batched weight iteration (one graph replay of the batched kernel, so requests that
+ * arrive while others run share the GPU), and a request leaves when its histogram is
+ * flat or it reached its max_iterations, freeing its memory for queued requests.  Each
+ * request's result equals that of muca_iterate_until_flat on the same instance alone.
+ * -------------------------------------------------------------------------------- */
+typedef struct muca_server_s *muca_server_t;
+
+#define MUCA_REQ_QUEUED 0
+#define MUCA_REQ_ACTIVE 1
+#define MUCA_REQ_DONE 2
+
+typedef struct {
+    int32_t L;                   /* one of 8, 16, 24, 32, 48, 64                           */
+    int64_t n_walkers;
+    uint64_t seed;
+    int32_t layout;              /* MUCA_LAYOUT_INT8 or MUCA_LAYOUT_PACKED                 */
+    int32_t walkers_per_block;   /* 0 = from occupancy                                     */
+    muca_params params;          /* fixed-sweep schedule                                   */
+} muca_request;
+
+typedef struct {
+    int32_t state;               /* MUCA_REQ_*                                             */
+    int32_t code;                /* when done: MUCA_OK (flat), MUCA_ENOTCONVERGED, error   */
+    muca_stats stats;            /* iterations, flatness, attempts; seconds while admitted */
+    double seconds_queued;       /* arrival -> admission (so far)                          */
+    double seconds_total;        /* arrival -> done: the time to converged weights         */
+} muca_request_status;
+
+/* Creates a server that keeps at most hbm_budget_bytes of instance device memory. */
+int muca_server_create(size_t hbm_budget_bytes, muca_server_t *out);
+int muca_server_destroy(muca_server_t s);
+
+/* Enqueues a request (arrival time = now) and returns its id.  Errors: MUCA_EINVAL
+ * (L not in the list, bad parameters), MUCA_ENOMEM (larger than the whole budget). */
+int muca_server_submit(muca_server_t s, const muca_request *r, int64_t *id);
+
+/* Admits what fits, runs one batched iteration of all admitted requests, retires the
+ * finished ones.  Reports the admitted and queued counts afterwards. */
+int muca_server_step(muca_server_t s, int32_t *n_active, int32_t *n_queued);
+
+/* State and timing of a request; its final ln W (n_bins = L*L + 1) once done. */
+int muca_server_status(muca_server_t s, int64_t id, muca_request_status *out);
+int muca_server_weights(muca_server_t s, int64_t id, double *lnW_out, size_t n_bins);
+
+/* Walker-attempts run so far, seconds since creation, steps, device bytes in use. */
+int muca_server_totals(muca_server_t s, uint64_t *walker_attempts, double *seconds, int32_t *steps,
+                       size_t *bytes_in_use);
+
+/* ----------------------------------------------------------------------------------
  * Allocation-free batched sweep.  The paper has no counterpart: this entry point exists
  * for callers that must not allocate device memory while they run, for instance an
  * application that owns the GPU's memory and lends out fixed buffers reserved at start-up,

@@ -52,6 +52,21 @@ class muca_stats(ctypes.Structure):
                 ("seconds", ctypes.c_double)]
 
 
+class muca_request(ctypes.Structure):
+    _fields_ = [("L", ctypes.c_int32), ("n_walkers", ctypes.c_int64), ("seed", ctypes.c_uint64),
+                ("layout", ctypes.c_int32), ("walkers_per_block", ctypes.c_int32), ("params", muca_params)]
+
+
+class muca_request_status(ctypes.Structure):
+    _fields_ = [("state", ctypes.c_int32), ("code", ctypes.c_int32), ("stats", muca_stats),
+                ("seconds_queued", ctypes.c_double), ("seconds_total", ctypes.c_double)]
+
+
+MUCA_REQ_QUEUED = 0
+MUCA_REQ_ACTIVE = 1
+MUCA_REQ_DONE = 2
+
+
 class muca_raw_instance(ctypes.Structure):
     _fields_ = [("L", ctypes.c_int32), ("layout", ctypes.c_int32), ("n_walkers", ctypes.c_int64),
                 ("seed", ctypes.c_uint64), ("t0", ctypes.c_uint64), ("lattice", ctypes.c_void_p),
@@ -97,6 +112,14 @@ SIGNATURES = {
     "muca_batch_sweep": (ctypes.c_int, [_H, ctypes.c_uint64, ctypes.c_int]),
     "muca_batch_iterate": (ctypes.c_int, [_H, _P(muca_params), _P(muca_stats)]),
     "muca_batch_info": (ctypes.c_int, [_H, _P(ctypes.c_int32), _P(ctypes.c_int32), _P(ctypes.c_size_t)]),
+    "muca_server_create": (ctypes.c_int, [ctypes.c_size_t, _P(_H)]),
+    "muca_server_destroy": (ctypes.c_int, [_H]),
+    "muca_server_submit": (ctypes.c_int, [_H, _P(muca_request), _P(ctypes.c_int64)]),
+    "muca_server_step": (ctypes.c_int, [_H, _P(ctypes.c_int32), _P(ctypes.c_int32)]),
+    "muca_server_status": (ctypes.c_int, [_H, ctypes.c_int64, _P(muca_request_status)]),
+    "muca_server_weights": (ctypes.c_int, [_H, ctypes.c_int64, _P(ctypes.c_double), ctypes.c_size_t]),
+    "muca_server_totals": (ctypes.c_int, [_H, _P(ctypes.c_uint64), _P(ctypes.c_double), _P(ctypes.c_int32),
+                                          _P(ctypes.c_size_t)]),
     "muca_batch_sweep_noalloc": (ctypes.c_int, [_P(muca_raw_instance), ctypes.c_int32, ctypes.c_uint64, ctypes.c_int,
                                                 ctypes.c_void_p]),
     "muca_last_error": (ctypes.c_char_p, []),

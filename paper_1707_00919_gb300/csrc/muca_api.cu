@@ -513,6 +513,90 @@ int build_graph(muca_batch_t b)
     return MUCA_OK;
 }
 
+
+int check_iteration_params(const muca_params &p, muca_t h)
+{
+    if (p.schedule != MUCA_SCHEDULE_SWEEPS)
+        return fail(MUCA_EINVAL, "batched iteration supports the fixed-sweep schedule");
+    if (p.stop_rule < MUCA_STOP_MIN_MEAN || p.stop_rule > MUCA_STOP_CHEBYSHEV || p.max_iterations < 1)
+        return fail(MUCA_EINVAL, "bad stop rule or max_iterations");
+    if (p.sweeps_per_iter * (uint64_t)h->N > 0xFFFFFFFFull / 256ull)
+        return fail(MUCA_EINVAL, "sweeps_per_iter too large for one recording launch");
+    if (h->t % (uint64_t)h->N != 0)
+        return fail(MUCA_EINVAL, "batched launches need every member at a sweep boundary");
+    return MUCA_OK;
+}
+
+// One weight iteration of the members `active` (indices into b->inst): member j
+// thermalizes therm[j] sweeps and records rec[j] sweeps, all members in one replay of
+// the iteration graph.  Afterwards each member's histogram is in its pinned buffer and
+// its attempt counter is advanced.
+int batch_run_iteration(muca_batch_t b, const std::vector<int32_t> &active, const std::vector<uint64_t> &therm,
+                        const std::vector<uint64_t> &rec)
+{
+    int rc = stage_wait(b);
+    if (rc)
+        return rc;
+    if (active != b->members || !b->exec) {
+        MUCA_CUDA(cudaStreamSynchronize(b->stream), "batch synchronize");
+        build_items(b, active);
+        rc = upload_items(b);
+        if (rc)
+            return rc;
+        MUCA_CUDA(cudaStreamSynchronize(b->stream), "batch synchronize");
+        rc = build_graph(b);
+        if (rc)
+            return rc;
+    }
+    const size_t nm = active.size();
+    for (size_t j = 0; j < nm; ++j) {
+        muca_t h = b->inst[(size_t)active[j]];
+        build_table(h->L, h->lnW, h->h_table);
+        const uint64_t nt = therm[j] * (uint64_t)h->N, nr = rec[j] * (uint64_t)h->N;
+        b->h_args[j] = make_args(h, h->t, nt);
+        b->h_args[nm + j] = make_args(h, h->t + nt, nr);
+        h->t += nt + nr;
+    }
+    MUCA_CUDA(cudaGraphLaunch(b->exec, b->stream), "batch iteration launch");
+    MUCA_CUDA(cudaStreamSynchronize(b->stream), "batch synchronize");
+    return check_members(b);
+}
+
+// Host half of one iteration for a member whose histogram is in its pinned buffer:
+// stop metric, flatness, Eq. (4) recursion.  Returns true when the member is finished
+// (flat, or max_iterations reached).
+bool member_update(muca_t h, const muca_params &p, muca_stats &s)
+{
+    const int32_t N = h->N;
+    std::vector<uint64_t> H(h->h_hist, h->h_hist + N + 1);
+    s.iterations += 1;
+    s.attempts_per_walker += (p.therm_sweeps + p.sweeps_per_iter) * (uint64_t)N;
+    double metric;
+    if (p.stop_rule == MUCA_STOP_MIN_MEAN)
+        metric = min_over_mean(N, H);
+    else if (p.stop_rule == MUCA_STOP_KL)
+        metric = kullback_leibler(N, H, (double)(N - 1));
+    else
+        metric = chebyshev(N, H);
+    s.last_metric = metric;
+    const bool flat = p.stop_rule == MUCA_STOP_MIN_MEAN ? metric >= p.flat_threshold : metric < p.flat_threshold;
+    if (flat) {
+        s.converged = 1;
+        return true;
+    }
+    for (int32_t e = 0; e <= N; ++e)
+        if (H[(size_t)e])
+            h->lnW[(size_t)e] -= std::log((double)H[(size_t)e]);
+    return s.iterations >= p.max_iterations;
+}
+
+size_t instance_device_bytes(int32_t L, int32_t layout, int64_t W)
+{
+    const size_t nb = (size_t)L * L + 1;
+    return align256(muca::lattice_bytes(L, layout == MUCA_LAYOUT_PACKED ? MUCA_LAYOUT_PACKED : MUCA_LAYOUT_INT8, W)) +
+           align256((size_t)W * sizeof(int32_t)) + align256(nb * 5 * sizeof(uint32_t)) +
+           align256(nb * sizeof(unsigned long long)) + 256;
+}
 }  // namespace
 
 extern "C" {
@@ -1182,84 +1266,30 @@ int muca_batch_iterate(muca_batch_t b, const muca_params *p_in, muca_stats *stat
         p = *p_in;
     else
         muca_default_params(&p);
-    if (p.schedule != MUCA_SCHEDULE_SWEEPS)
-        return fail(MUCA_EINVAL, "batched iteration supports the fixed-sweep schedule");
-    if (p.stop_rule < MUCA_STOP_MIN_MEAN || p.stop_rule > MUCA_STOP_CHEBYSHEV || p.max_iterations < 1)
-        return fail(MUCA_EINVAL, "bad stop rule or max_iterations");
+    const size_t n = b->inst.size();
     for (muca_t h : b->inst) {
-        if ((p.sweeps_per_iter * (uint64_t)h->N) > 0xFFFFFFFFull / 256ull)
-            return fail(MUCA_EINVAL, "sweeps_per_iter too large for one recording launch");
-        if (h->t % (uint64_t)h->N != 0)
-            return fail(MUCA_EINVAL, "batched launches need every member at a sweep boundary");
+        int rc = check_iteration_params(p, h);
+        if (rc)
+            return rc;
     }
     const auto start = std::chrono::steady_clock::now();
-    const size_t n = b->inst.size();
     std::vector<muca_stats> st(n);
     std::memset(st.data(), 0, sizeof(muca_stats) * n);
     std::vector<int32_t> active(n);
     for (size_t i = 0; i < n; ++i)
         active[i] = (int32_t)i;
-    int rc = stage_wait(b);
-    if (rc)
-        return rc;
-    MUCA_CUDA(cudaStreamSynchronize(b->stream), "batch synchronize");
     bool timed_out = false;
-    std::vector<uint64_t> H;
     while (!active.empty()) {
-        if (active != b->members || !b->exec || b->g_therm != p.therm_sweeps || b->g_rec != p.sweeps_per_iter) {
-            build_items(b, active);
-            rc = upload_items(b);
-            if (rc)
-                return rc;
-            MUCA_CUDA(cudaStreamSynchronize(b->stream), "batch synchronize");
-            rc = build_graph(b);
-            if (rc)
-                return rc;
-            b->g_therm = p.therm_sweeps;
-            b->g_rec = p.sweeps_per_iter;
-        }
-        const size_t nm = active.size();
-        for (size_t j = 0; j < nm; ++j) {
-            muca_t h = b->inst[(size_t)active[j]];
-            build_table(h->L, h->lnW, h->h_table);
-            const uint64_t nt = p.therm_sweeps * (uint64_t)h->N, nr = p.sweeps_per_iter * (uint64_t)h->N;
-            b->h_args[j] = make_args(h, h->t, nt);
-            b->h_args[nm + j] = make_args(h, h->t + nt, nr);
-            h->t += nt + nr;
-        }
-        MUCA_CUDA(cudaGraphLaunch(b->exec, b->stream), "batch iteration launch");
-        MUCA_CUDA(cudaStreamSynchronize(b->stream), "batch synchronize");
-        rc = check_members(b);
+        std::vector<uint64_t> therm(active.size(), p.therm_sweeps), rec(active.size(), p.sweeps_per_iter);
+        int rc = batch_run_iteration(b, active, therm, rec);
         if (rc)
             return rc;
         const double now = std::chrono::duration<double>(std::chrono::steady_clock::now() - start).count();
         std::vector<int32_t> next;
-        for (size_t j = 0; j < nm; ++j) {
-            const int32_t i = active[j];
-            muca_t h = b->inst[(size_t)i];
-            const int32_t N = h->N;
-            H.assign(h->h_hist, h->h_hist + N + 1);
+        for (int32_t i : active) {
             muca_stats &s = st[(size_t)i];
-            s.iterations += 1;
-            s.attempts_per_walker += (p.therm_sweeps + p.sweeps_per_iter) * (uint64_t)N;
-            double metric;
-            if (p.stop_rule == MUCA_STOP_MIN_MEAN)
-                metric = min_over_mean(N, H);
-            else if (p.stop_rule == MUCA_STOP_KL)
-                metric = kullback_leibler(N, H, (double)(N - 1));
-            else
-                metric = chebyshev(N, H);
-            s.last_metric = metric;
             s.seconds = now;
-            const bool flat = p.stop_rule == MUCA_STOP_MIN_MEAN ? metric >= p.flat_threshold : metric < p.flat_threshold;
-            if (flat) {
-                s.converged = 1;
-                continue;
-            }
-            for (int32_t e = 0; e <= N; ++e)
-                if (H[(size_t)e])
-                    h->lnW[(size_t)e] -= std::log((double)H[(size_t)e]);
-            if (s.iterations < p.max_iterations)
+            if (!member_update(b->inst[(size_t)i], p, s))
                 next.push_back(i);
         }
         active.swap(next);
@@ -1270,7 +1300,7 @@ int muca_batch_iterate(muca_batch_t b, const muca_params *p_in, muca_stats *stat
     }
     // device tables follow the host weights again
     for (muca_t h : b->inst) {
-        rc = upload_table(h);
+        int rc = upload_table(h);
         if (rc)
             return rc;
     }
@@ -1288,7 +1318,38 @@ int muca_batch_iterate(muca_batch_t b, const muca_params *p_in, muca_stats *stat
     return fail(MUCA_ENOTCONVERGED, "not every instance became flat");
 }
 
+}  // extern "C"
 
+// ---------------------------------------------------------------------------------
+// Serving: requests for whole weight iterations arrive over time; they are admitted
+// while their device memory fits the budget, their state stays resident, and every
+// step advances all admitted requests by one batched iteration.  Finished requests
+// free their memory for the next ones (continuous batching).
+// ---------------------------------------------------------------------------------
+struct ServerRequest {
+    muca_request req;
+    double t_arrival = 0.0, t_admit = -1.0, t_done = -1.0;
+    int32_t state = MUCA_REQ_QUEUED;
+    int32_t code = MUCA_OK;
+    size_t bytes = 0;
+    muca_t h = nullptr;
+    muca_stats st{};
+    std::vector<double> lnW;
+};
+
+struct muca_server_s {
+    size_t budget = 0, used = 0;
+    std::vector<ServerRequest> reqs;
+    std::vector<int64_t> queue;       // queued ids in arrival order
+    std::vector<int64_t> active;      // admitted ids
+    muca_batch_t batch = nullptr;
+    std::vector<int64_t> batch_ids;   // members of `batch`, in order
+    std::chrono::steady_clock::time_point t0;
+    uint64_t attempts = 0;            // walker-attempts run by the server
+    int32_t steps = 0;
+};
+
+extern "C" {
 int muca_batch_sweep_noalloc(const muca_raw_instance *instances, int32_t n, uint64_t n_sweeps, int record,
                              void *cuda_stream)
 {
@@ -1338,6 +1399,203 @@ int muca_batch_sweep_noalloc(const muca_raw_instance *instances, int32_t n, uint
     }
     MUCA_CUDA(muca::launch_batch_noalloc(descs, wpbs, n, smem, record != 0, static_cast<cudaStream_t>(cuda_stream)),
               "allocation-free batched sweep");
+    return MUCA_OK;
+}
+
+
+static double server_now(muca_server_t s)
+{
+    return std::chrono::duration<double>(std::chrono::steady_clock::now() - s->t0).count();
+}
+
+int muca_server_create(size_t hbm_budget_bytes, muca_server_t *out)
+{
+    if (!out || hbm_budget_bytes == 0)
+        return fail(MUCA_EINVAL, "server needs a memory budget");
+    muca_server_s *s = new (std::nothrow) muca_server_s;
+    if (!s)
+        return fail(MUCA_ENOMEM, "host allocation failed");
+    s->budget = hbm_budget_bytes;
+    s->t0 = std::chrono::steady_clock::now();
+    *out = s;
+    return MUCA_OK;
+}
+
+int muca_server_destroy(muca_server_t s)
+{
+    if (!s)
+        return MUCA_OK;
+    muca_batch_destroy(s->batch);
+    for (ServerRequest &r : s->reqs)
+        muca_destroy(r.h);
+    delete s;
+    return MUCA_OK;
+}
+
+int muca_server_submit(muca_server_t s, const muca_request *r, int64_t *id)
+{
+    if (!s || !r || !id)
+        return fail(MUCA_EINVAL, "NULL argument");
+    if (!batchable_L(r->L))
+        return fail(MUCA_EINVAL, "L = %d not in {8, 16, 24, 32, 48, 64}", r->L);
+    if (r->n_walkers < 1 || r->n_walkers > INT32_MAX)
+        return fail(MUCA_EINVAL, "n_walkers out of range");
+    if (r->layout == MUCA_LAYOUT_AUTO || r->walkers_per_block == MUCA_WPB_TUNE)
+        return fail(MUCA_EINVAL, "requests take an explicit layout and block size (0 = default)");
+    if (r->params.schedule != MUCA_SCHEDULE_SWEEPS || r->params.max_iterations < 1 ||
+        r->params.stop_rule < MUCA_STOP_MIN_MEAN || r->params.stop_rule > MUCA_STOP_CHEBYSHEV ||
+        r->params.sweeps_per_iter * (uint64_t)r->L * (uint64_t)r->L > 0xFFFFFFFFull / 256ull)
+        return fail(MUCA_EINVAL, "request parameters: fixed-sweep schedule, valid stop rule and sweeps");
+    ServerRequest q;
+    q.req = *r;
+    q.t_arrival = server_now(s);
+    q.bytes = instance_device_bytes(r->L, r->layout, r->n_walkers);
+    if (q.bytes > s->budget)
+        return fail(MUCA_ENOMEM, "request needs %zu bytes, more than the whole budget", q.bytes);
+    *id = (int64_t)s->reqs.size();
+    s->reqs.push_back(std::move(q));
+    s->queue.push_back(*id);
+    return MUCA_OK;
+}
+
+int muca_server_step(muca_server_t s, int32_t *n_active, int32_t *n_queued)
+{
+    if (!s)
+        return fail(MUCA_EINVAL, "NULL server");
+    // admission: every queued request that fits the remaining budget, in arrival order
+    std::vector<int64_t> still;
+    for (int64_t id : s->queue) {
+        ServerRequest &q = s->reqs[(size_t)id];
+        if (s->used + q.bytes > s->budget) {
+            still.push_back(id);
+            continue;
+        }
+        muca_options o;
+        std::memset(&o, 0, sizeof o);
+        o.L = q.req.L;
+        o.n_walkers = q.req.n_walkers;
+        o.seed = q.req.seed;
+        o.layout = q.req.layout;
+        o.walkers_per_block = q.req.walkers_per_block;
+        int rc = muca_create_ex(&o, &q.h);
+        if (rc == MUCA_ENOMEM) {
+            still.push_back(id);
+            continue;
+        }
+        if (rc != MUCA_OK) {
+            q.state = MUCA_REQ_DONE;
+            q.code = rc;
+            q.t_done = server_now(s);
+            continue;
+        }
+        q.state = MUCA_REQ_ACTIVE;
+        q.t_admit = server_now(s);
+        s->used += q.bytes;
+        s->active.push_back(id);
+    }
+    s->queue.swap(still);
+    if (!s->active.empty()) {
+        if (s->active != s->batch_ids) {
+            muca_batch_destroy(s->batch);
+            s->batch = nullptr;
+            std::vector<muca_t> hs;
+            for (int64_t id : s->active)
+                hs.push_back(s->reqs[(size_t)id].h);
+            int rc = muca_batch_create(hs.data(), (int32_t)hs.size(), &s->batch);
+            if (rc)
+                return rc;
+            s->batch_ids = s->active;
+        }
+        const size_t na = s->active.size();
+        std::vector<int32_t> members(na);
+        std::vector<uint64_t> therm(na), rec(na);
+        for (size_t j = 0; j < na; ++j) {
+            const ServerRequest &q = s->reqs[(size_t)s->active[j]];
+            members[j] = (int32_t)j;
+            therm[j] = q.req.params.therm_sweeps;
+            rec[j] = q.req.params.sweeps_per_iter;
+        }
+        int rc = batch_run_iteration(s->batch, members, therm, rec);
+        if (rc)
+            return rc;
+        s->steps += 1;
+        const double now = server_now(s);
+        std::vector<int64_t> next;
+        for (size_t j = 0; j < na; ++j) {
+            ServerRequest &q = s->reqs[(size_t)s->active[j]];
+            s->attempts += (therm[j] + rec[j]) * (uint64_t)q.h->N * (uint64_t)q.h->W;
+            q.st.seconds = now - q.t_admit;
+            if (!member_update(q.h, q.req.params, q.st)) {
+                next.push_back(s->active[j]);
+                continue;
+            }
+            q.state = MUCA_REQ_DONE;
+            q.code = q.st.converged ? MUCA_OK : MUCA_ENOTCONVERGED;
+            q.t_done = now;
+            q.lnW = q.h->lnW;
+        }
+        if (next.size() != s->active.size()) {
+            // finished requests leave: drop the batch first, then free their memory
+            muca_batch_destroy(s->batch);
+            s->batch = nullptr;
+            s->batch_ids.clear();
+            for (int64_t id : s->active) {
+                ServerRequest &q = s->reqs[(size_t)id];
+                if (q.state == MUCA_REQ_DONE) {
+                    muca_destroy(q.h);
+                    q.h = nullptr;
+                    s->used -= q.bytes;
+                }
+            }
+            s->active.swap(next);
+        }
+    }
+    if (n_active)
+        *n_active = (int32_t)s->active.size();
+    if (n_queued)
+        *n_queued = (int32_t)s->queue.size();
+    return MUCA_OK;
+}
+
+int muca_server_status(muca_server_t s, int64_t id, muca_request_status *out)
+{
+    if (!s || !out || id < 0 || id >= (int64_t)s->reqs.size())
+        return fail(MUCA_EINVAL, "unknown request");
+    const ServerRequest &q = s->reqs[(size_t)id];
+    out->state = q.state;
+    out->code = q.code;
+    out->stats = q.st;
+    const double now = server_now(s);
+    out->seconds_queued = (q.t_admit >= 0.0 ? q.t_admit : now) - q.t_arrival;
+    out->seconds_total = (q.t_done >= 0.0 ? q.t_done : now) - q.t_arrival;
+    return MUCA_OK;
+}
+
+int muca_server_weights(muca_server_t s, int64_t id, double *lnW_out, size_t n_bins)
+{
+    if (!s || !lnW_out || id < 0 || id >= (int64_t)s->reqs.size())
+        return fail(MUCA_EINVAL, "unknown request");
+    const ServerRequest &q = s->reqs[(size_t)id];
+    if (q.state != MUCA_REQ_DONE || q.lnW.empty())
+        return fail(MUCA_EINVAL, "request %lld has no final weights", (long long)id);
+    if (n_bins != q.lnW.size())
+        return fail(MUCA_EINVAL, "weights have %zu bins", q.lnW.size());
+    std::copy(q.lnW.begin(), q.lnW.end(), lnW_out);
+    return MUCA_OK;
+}
+
+int muca_server_totals(muca_server_t s, uint64_t *walker_attempts, double *seconds, int32_t *steps, size_t *bytes_in_use)
+{
+    if (!s)
+        return fail(MUCA_EINVAL, "NULL server");
+    if (walker_attempts)
+        *walker_attempts = s->attempts;
+    if (seconds)
+        *seconds = server_now(s);
+    if (steps)
+        *steps = s->steps;
+    if (bytes_in_use)
+        *bytes_in_use = s->used;
     return MUCA_OK;
 }
 

@@ -361,3 +361,60 @@ def muca_batch_sweep_noalloc(instances, n_sweeps: int, record: bool, stream_hand
     arr = (C.muca_raw_instance * len(instances))(*instances)
     _check(C.load().muca_batch_sweep_noalloc(arr, len(instances), n_sweeps, 1 if record else 0,
                                              ctypes.c_void_p(stream_handle or 0)))
+
+
+# ---------------------------------------------------------------------------------
+# serving
+# ---------------------------------------------------------------------------------
+class Server:
+    """Continuous batching of weight-iteration requests (muca_server_* in muca.h)."""
+
+    def __init__(self, hbm_budget_bytes: int):
+        use_torch_allocator()
+        self._s = ctypes.c_void_p()
+        _check(C.load().muca_server_create(int(hbm_budget_bytes), ctypes.byref(self._s)))
+
+    def submit(self, L: int, n_walkers: int, seed: int, params: muca_params, layout: int = MUCA_LAYOUT_INT8,
+               walkers_per_block: int = 0) -> int:
+        r = C.muca_request(L, n_walkers, seed, layout, walkers_per_block, params)
+        rid = ctypes.c_int64()
+        _check(C.load().muca_server_submit(self._s, ctypes.byref(r), ctypes.byref(rid)))
+        return rid.value
+
+    def step(self):
+        a, q = ctypes.c_int32(), ctypes.c_int32()
+        _check(C.load().muca_server_step(self._s, ctypes.byref(a), ctypes.byref(q)))
+        return a.value, q.value
+
+    def status(self, rid: int) -> C.muca_request_status:
+        st = C.muca_request_status()
+        _check(C.load().muca_server_status(self._s, rid, ctypes.byref(st)))
+        return st
+
+    def weights(self, rid: int, n_bins: int) -> np.ndarray:
+        a = np.zeros(n_bins, dtype=np.float64)
+        _check(C.load().muca_server_weights(self._s, rid, _p(a, ctypes.c_double), n_bins))
+        return a
+
+    def totals(self):
+        att, sec, steps, used = ctypes.c_uint64(), ctypes.c_double(), ctypes.c_int32(), ctypes.c_size_t()
+        _check(C.load().muca_server_totals(self._s, ctypes.byref(att), ctypes.byref(sec), ctypes.byref(steps),
+                                           ctypes.byref(used)))
+        return att.value, sec.value, steps.value, used.value
+
+    def close(self) -> None:
+        if self._s:
+            _check(C.load().muca_server_destroy(self._s))
+            self._s = None
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

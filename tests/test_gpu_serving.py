@@ -1,0 +1,74 @@
+"""Serving with continuous batching: requests of different L and walker counts arrive
+while others run, are admitted under a memory budget and iterated together; each result
+must equal the same request run alone (muca_iterate_until_flat), bit for bit."""
+import numpy as np
+import pytest
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def M():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import __graft_entry__
+    __graft_entry__.build()
+    from paper_1707_00919_gb300 import muca
+    return muca
+
+
+SPECS = [(8, 128, 1, 100), (16, 1024, 2, 40), (8, 256, 3, 100), (24, 2048, 4, 20), (16, 512, 5, 60),
+         (32, 4096, 6, 10)]
+
+
+def params(M, S):
+    return M.make_params(therm_sweeps=31, sweeps_per_iter=S, max_iterations=400)
+
+
+def test_requests_alone_and_in_the_mix_agree(M):
+    alone = []
+    for L, W, seed, S in SPECS:
+        with M.Muca(L, W, seed) as m:
+            st = m.iterate_until_flat(params(M, S))
+            alone.append((st, m.get_weights()))
+    # the L = 32 request (4.24 MB on the device) fits this budget only once the L = 24
+    # request (1.2 MB) has left, so it arrives while others run and has to wait
+    budget = 4_300_000
+    with M.Server(budget) as srv:
+        ids = []
+        arrivals = {0: [0, 1], 2: [2], 3: [3, 4], 6: [5]}   # step -> requests arriving before it
+        step = 0
+        max_queue = 0
+        while True:
+            for k in arrivals.get(step, []):
+                L, W, seed, S = SPECS[k]
+                ids.append((k, srv.submit(L, W, seed, params(M, S))))
+            active, queued = srv.step()
+            max_queue = max(max_queue, queued)
+            step += 1
+            if step > 7 and active == 0 and queued == 0:
+                break
+            assert step < 5000
+        assert max_queue >= 1                           # admission really waited for memory
+        for k, rid in ids:
+            L, W, seed, S = SPECS[k]
+            st = srv.status(rid)
+            assert st.state == M.C.MUCA_REQ_DONE
+            ref, lnW = alone[k]
+            assert st.stats.iterations == ref.iterations
+            assert bool(st.stats.converged) == ref.converged
+            assert st.stats.last_metric == ref.last_metric
+            assert np.array_equal(srv.weights(rid, L * L + 1), lnW)
+            assert st.seconds_total >= st.seconds_queued >= 0.0
+        att, sec, steps, used = srv.totals()
+        assert used == 0 and att > 0
+
+
+def test_server_rejects_bad_requests(M):
+    with M.Server(1 << 20) as srv:
+        with pytest.raises(M.MucaError):
+            srv.submit(12, 64, 1, params(M, 10))                  # no whole-sweep kernel
+        with pytest.raises(M.MucaError) as ex:
+            srv.submit(64, 1 << 20, 1, params(M, 1))              # larger than the budget
+        assert ex.value.code == M.C.MUCA_ENOMEM
