@@ -397,6 +397,154 @@ def run_reference(args):
     print(json.dumps(out))
 
 
+# ----------------------------------------------------------------------------------
+# extra workloads: the 24-instance batched mix and the served request stream
+# ----------------------------------------------------------------------------------
+def mix_specs():
+    """Configuration 4: 24 instances, L from {16, 24, 32, 48, 64}, walkers uniform in
+    512..16384 (seed 1234), instance seeds 1234 + index."""
+    import numpy as np
+    rng = np.random.default_rng(1234)
+    Ls = rng.choice([16, 24, 32, 48, 64], size=24)
+    Ws = rng.integers(512, 16385, size=24)
+    return [(int(L), int(W), 1234 + i) for i, (L, W) in enumerate(zip(Ls, Ws))]
+
+
+def run_batch_workload(args):
+    """Aggregate attempts/s of the 24-instance mix: each instance iterated alone, one
+    after the other (one launch per instance and phase), against all instances in the
+    batched persistent kernel (one graph replay per iteration).  Both run the same
+    number of weight iterations on identical state, so their results are identical."""
+    import numpy as np
+    import torch
+    import __graft_entry__
+    __graft_entry__.build()
+    from paper_1707_00919_gb300 import muca as M
+    iters = max(1, args.steps)
+    specs = mix_specs()
+    p = M.make_params(therm_sweeps=THERM_SWEEPS, sweeps_per_iter=SWEEPS_PER_ITER, max_iterations=iters,
+                      flat_threshold=2.0)
+    attempts = sum(W * L * L * (THERM_SWEEPS + SWEEPS_PER_ITER) * iters for L, W, _ in specs)
+    # plain path
+    inst = [M.Muca(L, W, seed) for L, W, seed in specs]
+    for m in inst:
+        m.sweep(1, record=False)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for m in inst:
+        m.iterate_until_flat(p)
+    torch.cuda.synchronize()
+    plain_s = time.perf_counter() - t0
+    plain_w = [m.get_weights() for m in inst]
+    for m in inst:
+        m.close()
+    # batched path
+    inst = [M.Muca(L, W, seed) for L, W, seed in specs]
+    for m in inst:
+        m.sweep(1, record=False)
+    torch.cuda.synchronize()
+    with M.Batch(inst) as b:
+        t0 = time.perf_counter()
+        b.iterate_until_flat(p)
+        torch.cuda.synchronize()
+        batch_s = time.perf_counter() - t0
+        n, grid, smem = b.info()
+    same = all(np.array_equal(m.get_weights(), w) for m, w in zip(inst, plain_w))
+    for m in inst:
+        m.close()
+    print(json.dumps({
+        "metric": "aggregate spin-flip attempts/s, 24-instance mix (L 16-64, 512-16384 walkers)",
+        "value": attempts / batch_s, "unit": "attempts/s", "n_gpus": 1, "higher_is_better": True,
+        "workload": "batched persistent kernel, one CUDA graph per weight iteration",
+        "iterations": iters, "plain_value": attempts / plain_s, "speedup_vs_plain": plain_s / batch_s,
+        "identical_results": same, "batch_grid": grid, "batch_smem_bytes": smem,
+        "config": {"instances": [{"L": L, "walkers": W} for L, W, _ in specs],
+                   "therm_sweeps": THERM_SWEEPS, "sweeps_per_iter": SWEEPS_PER_ITER},
+        "data": "synthetic"}))
+
+
+def serve_sweeps(L, W, target=50000):
+    """Recorded sweeps per iteration giving about `target` counts per energy."""
+    N = L * L
+    return max(1, -(-target * (N + 1) // (W * N)))
+
+
+def run_serve_workload(args):
+    """Configuration 5: Poisson arrivals (mean 20 per second, seed 7) of weight-iteration
+    requests, L uniform over {8, 16, 24, 32, 48, 64}, walkers from {256, 1024, 4096,
+    16384}, admitted under a 150 GB budget; reports p50 / p99 time from arrival to
+    converged weights and aggregate attempts/s, against a first-come-first-served queue
+    of the same requests run one at a time (its latencies computed from each request's
+    measured time alone and the same arrival times)."""
+    import numpy as np
+    import torch
+    import __graft_entry__
+    __graft_entry__.build()
+    from paper_1707_00919_gb300 import muca as M
+    rng = np.random.default_rng(7)
+    horizon = float(args.serve_seconds)
+    t, reqs = 0.0, []
+    while True:
+        t += rng.exponential(1.0 / 20.0)
+        if t > horizon:
+            break
+        L = int(rng.choice([8, 16, 24, 32, 48, 64]))
+        W = int(rng.choice([256, 1024, 4096, 16384]))
+        reqs.append((t, L, W, 7000 + len(reqs)))
+    params = {i: M.make_params(therm_sweeps=THERM_SWEEPS, sweeps_per_iter=serve_sweeps(L, W), max_iterations=2000)
+              for i, (_, L, W, _) in enumerate(reqs)}
+    # served
+    srv = M.Server(150 * 10**9)
+    start = time.perf_counter()
+    ids = {}
+    k = 0
+    while True:
+        now = time.perf_counter() - start
+        while k < len(reqs) and reqs[k][0] <= now:
+            _, L, W, seed = reqs[k]
+            ids[k] = srv.submit(L, W, seed, params[k])
+            k += 1
+        active, queued = srv.step()
+        if k == len(reqs) and active == 0 and queued == 0:
+            break
+        if active == 0 and queued == 0 and k < len(reqs):
+            time.sleep(max(0.0, min(0.01, reqs[k][0] - (time.perf_counter() - start))))
+    wall = time.perf_counter() - start
+    att, _, steps, _ = srv.totals()
+    lat = np.array([srv.status(ids[i]).seconds_total for i in range(len(reqs))])
+    conv = np.mean([srv.status(ids[i]).stats.converged for i in range(len(reqs))])
+    srv.close()
+    # plain: each request alone, first come first served
+    service, attempts_plain = [], 0
+    for i, (_, L, W, seed) in enumerate(reqs):
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        with M.Muca(L, W, seed) as m:
+            st = m.iterate_until_flat(params[i])
+        torch.cuda.synchronize()
+        service.append(time.perf_counter() - t0)
+        attempts_plain += st.attempts_per_walker * W
+    free_at, lat_plain = 0.0, []
+    for (arr, _, _, _), s in zip(reqs, service):
+        begin = max(arr, free_at)
+        free_at = begin + s
+        lat_plain.append(free_at - arr)
+    lat_plain = np.array(lat_plain)
+    print(json.dumps({
+        "metric": "time from arrival to converged weights (p50/p99) and aggregate attempts/s, served stream",
+        "value": float(np.percentile(lat, 50)), "unit": "s", "higher_is_better": False, "n_gpus": 1,
+        "p50_s": float(np.percentile(lat, 50)), "p99_s": float(np.percentile(lat, 99)),
+        "aggregate_attempts_per_s": att / wall, "requests": len(reqs), "converged_fraction": float(conv),
+        "steps": steps, "wall_s": wall,
+        "plain": {"p50_s": float(np.percentile(lat_plain, 50)), "p99_s": float(np.percentile(lat_plain, 99)),
+                  "aggregate_attempts_per_s": attempts_plain / sum(service), "busy_s": sum(service)},
+        "config": {"arrival_rate_per_s": 20, "arrival_seconds": horizon, "L": [8, 16, 24, 32, 48, 64],
+                   "walkers": [256, 1024, 4096, 16384], "budget_bytes": 150 * 10**9,
+                   "sweeps_per_iter": "ceil(50000 (N+1) / (W N))", "therm_sweeps": THERM_SWEEPS,
+                   "max_iterations": 2000},
+        "data": "synthetic"}))
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -404,7 +552,15 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["native", "reference"], default="native")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--workload", choices=["headline", "batch", "serve"], default="headline")
+    ap.add_argument("--serve-seconds", type=float, default=2.0)
     args = ap.parse_args()
+    if args.workload == "batch":
+        run_batch_workload(args)
+        return
+    if args.workload == "serve":
+        run_serve_workload(args)
+        return
     if args.warmup < 3 and args.impl == "native":
         args.warmup = 3
     if args.impl == "reference":
