@@ -184,6 +184,22 @@ int muca_iterate_until_flat(muca_t h, const muca_params *p, muca_stats *stats);
 int muca_production(muca_t h, uint64_t therm_sweeps, uint64_t n_sweeps, uint64_t *H_out,
                     double *ln_g_out, size_t n_bins);
 
+/* Production with error bars (Sec. 3.3): thermalize, then n_chunks >= 2 recorded
+ * chunks of sweeps_per_chunk sweeps, each with its own histogram (H_chunks_out, may be
+ * NULL, receives them as [chunk][bin]).  ln_g_out is the estimate from all chunks
+ * (as muca_production); ln_g_err_out the jackknife error over leave-one-chunk-out
+ * estimates, sqrt((n-1)/n sum_c (x_c - mean)^2), +inf where an energy is missing from
+ * some leave-one-out histogram and NaN where it was never visited. */
+int muca_production_jackknife(muca_t h, uint64_t therm_sweeps, int32_t n_chunks, uint64_t sweeps_per_chunk,
+                              uint64_t *H_chunks_out, double *ln_g_out, double *ln_g_err_out, size_t n_bins);
+
+/* Reweighting ln g (n_bins = L*L + 1, -inf entries skipped) to the canonical ensemble,
+ * P(E) ~ g(E) exp(-beta E) (Eq. 1): energy per spin <E>/N and specific heat per spin
+ * beta^2 (<E^2> - <E>^2)/N (may be NULL) at each of n_betas inverse temperatures.
+ * Host-only arithmetic in FP64 (log-sum-exp); no instance or GPU needed. */
+int muca_reweight(int32_t L, const double *ln_g, size_t n_bins, const double *betas, size_t n_betas,
+                  double *energy_per_spin, double *specific_heat_per_spin);
+
 /* Copies the walkers' energy indices (int32, n = n_walkers).  Syncs. */
 int muca_get_energies(muca_t h, int32_t *e_out, size_t n);
 

@@ -500,3 +500,97 @@ int32_t orc_production(int32_t L, int64_t nw, uint64_t seed, int8_t *spins, int3
     free(T);
     return 0;
 }
+
+/* ---------------------------------------------------------------------------------
+ * Jackknife errors of the production estimate (Sec. 3.3): the recorded updates are
+ * split into n chunks with histograms Hc[c][e]; estimate c leaves chunk c out,
+ * ln g_(c) = normalised ln(H - Hc[c]) - ln W, and the error of ln g(e) is
+ * sqrt((n - 1)/n sum_c (ln g_(c)(e) - mean_c ln g_(c)(e))^2).  ln_g receives the
+ * estimate from all chunks.  Energies missing from some leave-one-out histogram get an
+ * infinite error; energies never visited get -inf and an error of NaN.
+ * ------------------------------------------------------------------------------- */
+int32_t orc_jackknife(int32_t L, const double *lnW, const uint64_t *Hc, int32_t n, double *ln_g, double *err)
+{
+    const int N = L * L;
+    const int B = N + 1;
+    uint64_t *tot = (uint64_t *)calloc((size_t)B, sizeof(uint64_t));
+    uint64_t *Hm = (uint64_t *)malloc(sizeof(uint64_t) * (size_t)B);
+    double *est = (double *)malloc(sizeof(double) * (size_t)B * (size_t)n);
+    if (!tot || !Hm || !est) {
+        free(tot);
+        free(Hm);
+        free(est);
+        return -1;
+    }
+    for (int c = 0; c < n; ++c)
+        for (int e = 0; e < B; ++e)
+            tot[e] += Hc[(size_t)c * B + e];
+    orc_ln_dos(L, lnW, tot, ln_g);
+    for (int c = 0; c < n; ++c) {
+        for (int e = 0; e < B; ++e)
+            Hm[e] = tot[e] - Hc[(size_t)c * B + e];
+        orc_ln_dos(L, lnW, Hm, est + (size_t)c * B);
+    }
+    for (int e = 0; e < B; ++e) {
+        if (tot[e] == 0u) {
+            err[e] = NAN;
+            continue;
+        }
+        double mean = 0.0;
+        int missing = 0;
+        for (int c = 0; c < n; ++c) {
+            double v = est[(size_t)c * B + e];
+            if (v == -INFINITY)
+                missing = 1;
+            mean += v;
+        }
+        if (missing) {
+            err[e] = INFINITY;
+            continue;
+        }
+        mean /= (double)n;
+        double s = 0.0;
+        for (int c = 0; c < n; ++c) {
+            double d = est[(size_t)c * B + e] - mean;
+            s += d * d;
+        }
+        err[e] = sqrt((double)(n - 1) / (double)n * s);
+    }
+    free(tot);
+    free(Hm);
+    free(est);
+    return 0;
+}
+
+/* ---------------------------------------------------------------------------------
+ * Reweighting to the canonical ensemble (Sec. 2.1, Sec. 3.3): with P(E) ~ g(E) e^{-beta E}
+ * (Eq. 1) from ln g on the energy grid E = -2N + 4e, the mean energy per spin <E>/N and
+ * the specific heat per spin beta^2 (<E^2> - <E>^2) / N, by log-sum-exp.
+ * ------------------------------------------------------------------------------- */
+void orc_canonical(int32_t L, const double *ln_g, double beta, double *e_per_spin, double *c_per_spin)
+{
+    const int N = L * L;
+    double m = -INFINITY;
+    for (int e = 0; e <= N; ++e) {
+        if (ln_g[e] == -INFINITY)
+            continue;
+        double E = -2.0 * N + 4.0 * e;
+        double v = ln_g[e] - beta * E;
+        if (v > m)
+            m = v;
+    }
+    double z = 0.0, s1 = 0.0, s2 = 0.0;
+    for (int e = 0; e <= N; ++e) {
+        if (ln_g[e] == -INFINITY)
+            continue;
+        double E = -2.0 * N + 4.0 * e;
+        double w = exp(ln_g[e] - beta * E - m);
+        z += w;
+        s1 += w * E;
+        s2 += w * E * E;
+    }
+    double mean = s1 / z;
+    double var = s2 / z - mean * mean;
+    *e_per_spin = mean / (double)N;
+    *c_per_spin = beta * beta * var / (double)N;
+}

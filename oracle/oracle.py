@@ -90,6 +90,8 @@ def lib():
                 "orc_production": (i32, [i32, i64, u64, P(i8), P(i32), P(dbl), P(u64), u64, u64,
                                          P(u64), P(dbl)]),
                 "orc_dos_bruteforce": (i32, [i32, P(u64)]),
+                "orc_jackknife": (i32, [i32, P(dbl), P(u64), i32, P(dbl), P(dbl)]),
+                "orc_canonical": (None, [i32, P(dbl), dbl, P(dbl), P(dbl)]),
                 "orc_dos_transfer": (i32, [i32, P(u64), P(u64)]),
             }
             for name, (res, args) in sig.items():
@@ -252,3 +254,24 @@ def dos_transfer(L: int) -> list[int]:
     if rc != 0:
         raise ValueError(f"transfer matrix failed ({rc})")
     return [int(a) | (int(b) << 64) for a, b in zip(lo, hi)]
+
+
+def jackknife(L: int, lnW: np.ndarray, Hc: np.ndarray):
+    """Hc: [n_chunks][N+1] uint64 -> (ln_g, err)."""
+    Hc = np.ascontiguousarray(Hc, dtype=np.uint64)
+    B = L * L + 1
+    ln_g = np.zeros(B)
+    err = np.zeros(B)
+    rc = lib().orc_jackknife(L, _ptr(np.ascontiguousarray(lnW, dtype=np.float64), ctypes.c_double),
+                             _ptr(Hc, ctypes.c_uint64), Hc.shape[0], _ptr(ln_g, ctypes.c_double),
+                             _ptr(err, ctypes.c_double))
+    if rc != 0:
+        raise MemoryError("orc_jackknife failed")
+    return ln_g, err
+
+
+def canonical(L: int, ln_g: np.ndarray, beta: float):
+    e, c = ctypes.c_double(), ctypes.c_double()
+    lib().orc_canonical(L, _ptr(np.ascontiguousarray(ln_g, dtype=np.float64), ctypes.c_double), beta,
+                        ctypes.byref(e), ctypes.byref(c))
+    return e.value, c.value

@@ -100,6 +100,11 @@ SIGNATURES = {
     "muca_iterate_until_flat": (ctypes.c_int, [_H, _P(muca_params), _P(muca_stats)]),
     "muca_production": (ctypes.c_int, [_H, ctypes.c_uint64, ctypes.c_uint64, _P(ctypes.c_uint64),
                                        _P(ctypes.c_double), ctypes.c_size_t]),
+    "muca_production_jackknife": (ctypes.c_int, [_H, ctypes.c_uint64, ctypes.c_int32, ctypes.c_uint64,
+                                                 _P(ctypes.c_uint64), _P(ctypes.c_double), _P(ctypes.c_double),
+                                                 ctypes.c_size_t]),
+    "muca_reweight": (ctypes.c_int, [ctypes.c_int32, _P(ctypes.c_double), ctypes.c_size_t, _P(ctypes.c_double),
+                                     ctypes.c_size_t, _P(ctypes.c_double), _P(ctypes.c_double)]),
     "muca_get_energies": (ctypes.c_int, [_H, _P(ctypes.c_int32), ctypes.c_size_t]),
     "muca_get_lattice": (ctypes.c_int, [_H, _P(ctypes.c_int8), ctypes.c_size_t]),
     "muca_get_info": (ctypes.c_int, [_H, _P(ctypes.c_int32), _P(ctypes.c_int64), _P(ctypes.c_uint64),

@@ -597,6 +597,27 @@ size_t instance_device_bytes(int32_t L, int32_t layout, int64_t W)
            align256((size_t)W * sizeof(int32_t)) + align256(nb * 5 * sizeof(uint32_t)) +
            align256(nb * sizeof(unsigned long long)) + 256;
 }
+
+// ln g(e) = ln H(e) - ln W(e) on visited energies, shifted so that sum_e exp(ln g) = 2^N
+// (Sec. 3.3); -inf elsewhere.
+void ln_dos_from_histogram(int32_t N, const std::vector<double> &lnW, const uint64_t *H, double *ln_g)
+{
+    double top = -INFINITY;
+    for (int32_t e = 0; e <= N; ++e) {
+        ln_g[e] = H[e] ? std::log((double)H[e]) - lnW[(size_t)e] : -INFINITY;
+        top = std::max(top, ln_g[e]);
+    }
+    if (top == -INFINITY)
+        return;
+    double s = 0.0;
+    for (int32_t e = 0; e <= N; ++e)
+        if (H[e])
+            s += std::exp(ln_g[e] - top);
+    const double shift = (double)N * std::log(2.0) - (top + std::log(s));
+    for (int32_t e = 0; e <= N; ++e)
+        if (H[e])
+            ln_g[e] += shift;
+}
 }  // namespace
 
 extern "C" {
@@ -991,21 +1012,7 @@ int muca_production(muca_t h, uint64_t therm_sweeps, uint64_t n_sweeps, uint64_t
     if (rc)
         return rc;
     // Sec. 3.3: ln g = ln H - ln W on visited energies, normalised to 2^N states.
-    double top = -INFINITY;
-    for (int32_t e = 0; e <= N; ++e) {
-        ln_g_out[e] = H[(size_t)e] ? std::log((double)H[(size_t)e]) - h->lnW[(size_t)e] : -INFINITY;
-        top = std::max(top, ln_g_out[e]);
-    }
-    if (top > -INFINITY) {
-        double s = 0.0;
-        for (int32_t e = 0; e <= N; ++e)
-            if (H[(size_t)e])
-                s += std::exp(ln_g_out[e] - top);
-        const double shift = (double)N * std::log(2.0) - (top + std::log(s));
-        for (int32_t e = 0; e <= N; ++e)
-            if (H[(size_t)e])
-                ln_g_out[e] += shift;
-    }
+    ln_dos_from_histogram(N, h->lnW, H.data(), ln_g_out);
     if (H_out)
         std::copy(H.begin(), H.end(), H_out);
     return MUCA_OK;
@@ -1596,6 +1603,112 @@ int muca_server_totals(muca_server_t s, uint64_t *walker_attempts, double *secon
         *steps = s->steps;
     if (bytes_in_use)
         *bytes_in_use = s->used;
+    return MUCA_OK;
+}
+
+
+int muca_production_jackknife(muca_t h, uint64_t therm_sweeps, int32_t n_chunks, uint64_t sweeps_per_chunk,
+                              uint64_t *H_chunks_out, double *ln_g_out, double *ln_g_err_out, size_t n_bins)
+{
+    int rc = validate(h);
+    if (rc)
+        return rc;
+    const int32_t N = h->N;
+    const size_t B = (size_t)N + 1;
+    if (!ln_g_out || !ln_g_err_out || n_bins != B)
+        return fail(MUCA_EINVAL, "ln g and its error need %d bins", N + 1);
+    if (n_chunks < 2 || sweeps_per_chunk == 0)
+        return fail(MUCA_EINVAL, "a jackknife needs at least two non-empty chunks");
+    rc = upload_table(h);
+    if (rc)
+        return rc;
+    rc = muca_sweep(h, therm_sweeps, 0);
+    if (rc)
+        return rc;
+    std::vector<uint64_t> chunks((size_t)n_chunks * B), total(B, 0), H;
+    for (int32_t c = 0; c < n_chunks; ++c) {
+        rc = muca_reset_histogram(h);
+        if (rc)
+            return rc;
+        rc = muca_sweep(h, sweeps_per_chunk, 1);
+        if (rc)
+            return rc;
+        rc = read_histogram(h, H);
+        if (rc)
+            return rc;
+        for (size_t e = 0; e < B; ++e) {
+            chunks[(size_t)c * B + e] = H[e];
+            total[e] += H[e];
+        }
+    }
+    // Sec. 3.3: leave-one-chunk-out estimates, error sqrt((n-1)/n sum (x_c - mean)^2)
+    ln_dos_from_histogram(N, h->lnW, total.data(), ln_g_out);
+    std::vector<double> loo((size_t)n_chunks * B);
+    std::vector<uint64_t> rest(B);
+    for (int32_t c = 0; c < n_chunks; ++c) {
+        for (size_t e = 0; e < B; ++e)
+            rest[e] = total[e] - chunks[(size_t)c * B + e];
+        ln_dos_from_histogram(N, h->lnW, rest.data(), loo.data() + (size_t)c * B);
+    }
+    for (size_t e = 0; e < B; ++e) {
+        if (!total[e]) {
+            ln_g_err_out[e] = NAN;
+            continue;
+        }
+        double mean = 0.0;
+        bool missing = false;
+        for (int32_t c = 0; c < n_chunks; ++c) {
+            const double v = loo[(size_t)c * B + e];
+            missing = missing || v == -INFINITY;
+            mean += v;
+        }
+        if (missing) {
+            ln_g_err_out[e] = INFINITY;
+            continue;
+        }
+        mean /= (double)n_chunks;
+        double ss = 0.0;
+        for (int32_t c = 0; c < n_chunks; ++c) {
+            const double d = loo[(size_t)c * B + e] - mean;
+            ss += d * d;
+        }
+        ln_g_err_out[e] = std::sqrt((double)(n_chunks - 1) / (double)n_chunks * ss);
+    }
+    if (H_chunks_out)
+        std::copy(chunks.begin(), chunks.end(), H_chunks_out);
+    return MUCA_OK;
+}
+
+int muca_reweight(int32_t L, const double *ln_g, size_t n_bins, const double *betas, size_t n_betas,
+                  double *energy_per_spin, double *specific_heat_per_spin)
+{
+    if (L < 2 || !ln_g || n_bins != (size_t)L * L + 1 || (n_betas && (!betas || !energy_per_spin)))
+        return fail(MUCA_EINVAL, "reweighting needs L*L+1 values of ln g and output arrays");
+    const int32_t N = L * L;
+    for (size_t b = 0; b < n_betas; ++b) {
+        const double beta = betas[b];
+        // Eq. (1): P(E) ~ g(E) exp(-beta E) on E = -2N + 4e, summed in log space
+        double top = -INFINITY;
+        for (int32_t e = 0; e <= N; ++e)
+            if (ln_g[e] != -INFINITY)
+                top = std::max(top, ln_g[e] - beta * (-2.0 * N + 4.0 * e));
+        if (top == -INFINITY)
+            return fail(MUCA_EINVAL, "ln g has no finite entry");
+        double z = 0.0, m1 = 0.0, m2 = 0.0;
+        for (int32_t e = 0; e <= N; ++e) {
+            if (ln_g[e] == -INFINITY)
+                continue;
+            const double E = -2.0 * N + 4.0 * e;
+            const double p = std::exp(ln_g[e] - beta * E - top);
+            z += p;
+            m1 += p * E;
+            m2 += p * E * E;
+        }
+        const double mean = m1 / z;
+        energy_per_spin[b] = mean / (double)N;
+        if (specific_heat_per_spin)
+            specific_heat_per_spin[b] = beta * beta * (m2 / z - mean * mean) / (double)N;
+    }
     return MUCA_OK;
 }
 

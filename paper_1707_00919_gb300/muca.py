@@ -151,6 +151,25 @@ def muca_production(h, therm_sweeps: int, n_sweeps: int, n_bins: int):
     return H, g
 
 
+def muca_production_jackknife(h, therm_sweeps: int, n_chunks: int, sweeps_per_chunk: int, n_bins: int):
+    Hc = np.zeros((n_chunks, n_bins), dtype=np.uint64)
+    g = np.zeros(n_bins)
+    err = np.zeros(n_bins)
+    _check(C.load().muca_production_jackknife(h, therm_sweeps, n_chunks, sweeps_per_chunk, _p(Hc, ctypes.c_uint64),
+                                              _p(g, ctypes.c_double), _p(err, ctypes.c_double), n_bins))
+    return Hc, g, err
+
+
+def muca_reweight(L: int, ln_g, betas):
+    g = np.ascontiguousarray(ln_g, dtype=np.float64)
+    b = np.ascontiguousarray(np.atleast_1d(betas), dtype=np.float64)
+    e = np.zeros(b.size)
+    c = np.zeros(b.size)
+    _check(C.load().muca_reweight(L, _p(g, ctypes.c_double), g.size, _p(b, ctypes.c_double), b.size,
+                                  _p(e, ctypes.c_double), _p(c, ctypes.c_double)))
+    return e, c
+
+
 def muca_get_energies(h, n_walkers: int) -> np.ndarray:
     a = np.zeros(n_walkers, dtype=np.int32)
     _check(C.load().muca_get_energies(h, _p(a, ctypes.c_int32), n_walkers))
@@ -270,6 +289,10 @@ class Muca:
 
     def production(self, therm_sweeps: int, n_sweeps: int):
         return muca_production(self._h, therm_sweeps, n_sweeps, self.n_bins)
+
+    def production_jackknife(self, therm_sweeps: int, n_chunks: int, sweeps_per_chunk: int):
+        """(chunk histograms, ln g, jackknife error of ln g)."""
+        return muca_production_jackknife(self._h, therm_sweeps, n_chunks, sweeps_per_chunk, self.n_bins)
 
     def get_energies(self) -> np.ndarray:
         return muca_get_energies(self._h, self.W)
