@@ -37,8 +37,10 @@
  *   R5 recursion: ln W(e) -= ln H(e) with raw counts, only where H(e) > 0.
  *   R6 accessible energies: every grid point except e = 1 and e = N - 1.
  *   R7 the KL reference distribution Q is uniform over the accessible energies inside
- *      the range covered in the previous iteration (at least 10 of them); the schedule
- *      width w is that range's extent e_max - e_min + 1.
+ *      the union of the range covered in the previous iteration and the range of the
+ *      histogram being tested (at least 10 of them), so that Q covers P's support and
+ *      d_k >= 0 as Sec. 3 states; the schedule width w is the previous range's extent
+ *      e_max - e_min + 1.
  */
 #include <math.h>
 #include <stdint.h>
@@ -290,6 +292,26 @@ int32_t orc_accessible_in_range(int32_t L, const uint64_t *H)
     return count;
 }
 
+/* Reading R7: accessible energies in the union of [prev_lo, prev_hi] (none if
+ * prev_lo < 0) and the visited range of H, at least 10. */
+int32_t orc_kl_support(int32_t L, int32_t prev_lo, int32_t prev_hi, const uint64_t *H)
+{
+    const int N = L * L;
+    int lo = prev_lo, hi = prev_hi;
+    for (int e = 0; e <= N; ++e)
+        if (H[e] > 0u) {
+            if (lo < 0 || e < lo)
+                lo = e;
+            if (hi < 0 || e > hi)
+                hi = e;
+        }
+    int count = 0;
+    if (lo >= 0)
+        for (int e = lo; e <= hi; ++e)
+            count += orc_accessible(L, e);
+    return count > 10 ? count : 10;
+}
+
 /* Kullback-Leibler divergence, Eq. (6): d_k = sum P ln(P/Q) with P = H / sum(H) and
  * Q = 1/q, empty bins contributing nothing. */
 double orc_kullback_leibler(int32_t L, const uint64_t *H, double q)
@@ -393,7 +415,7 @@ int32_t orc_iterate(int32_t L, int64_t nw, uint64_t seed, int8_t *spins, int32_t
     uint64_t t = *t_inout;
     uint64_t spent = 0;
     int32_t prev_width = 0;      /* width covered in the previous iteration */
-    int32_t prev_accessible = 0; /* accessible energies inside that range   */
+    int32_t prev_lo = -1, prev_hi = -1;   /* that range                       */
     int full = 0;                /* the whole range has been covered        */
     uint64_t n_upd_prev = 0;
     int32_t n = 0;
@@ -401,11 +423,9 @@ int32_t orc_iterate(int32_t L, int64_t nw, uint64_t seed, int8_t *spins, int32_t
     double metric = 0.0;
     while (n < p->max_iterations) {
         uint64_t n_therm, n_upd;
-        double q;
         if (p->schedule == 0) {
             n_therm = p->therm_sweeps * (uint64_t)N;
             n_upd = p->sweeps_per_iter * (uint64_t)N;
-            q = (double)(N - 1);
         } else {
             int32_t w = prev_width > 10 ? prev_width : 10;
             n_therm = (uint64_t)(p->f_therm * (double)w);
@@ -417,7 +437,6 @@ int32_t orc_iterate(int32_t L, int64_t nw, uint64_t seed, int8_t *spins, int32_t
                 if (prev_width == N + 1)
                     full = 1;
             }
-            q = (double)(prev_accessible > 10 ? prev_accessible : 10);
         }
         if (lnW_history)
             memcpy(lnW_history + (size_t)n * (N + 1), lnW, sizeof(double) * (N + 1));
@@ -428,6 +447,7 @@ int32_t orc_iterate(int32_t L, int64_t nw, uint64_t seed, int8_t *spins, int32_t
         orc_run(L, seed, 0u, nw, spins, e, T, t, n_upd, 1, H);
         t += n_upd;
         spent += n_therm + n_upd;
+        const double q = (double)orc_kl_support(L, prev_lo, prev_hi, H);
         metric = orc_stop_metric(L, H, p->stop_rule, q);
         if (metric_history)
             metric_history[n] = metric;
@@ -438,7 +458,14 @@ int32_t orc_iterate(int32_t L, int64_t nw, uint64_t seed, int8_t *spins, int32_t
         }
         orc_update_weights(L, lnW, H);
         prev_width = orc_width(L, H);
-        prev_accessible = orc_accessible_in_range(L, H);
+        prev_lo = -1;
+        prev_hi = -1;
+        for (int e = 0; e <= N; ++e)
+            if (H[e] > 0u) {
+                if (prev_lo < 0)
+                    prev_lo = e;
+                prev_hi = e;
+            }
         n_upd_prev = n_upd;
     }
     *t_inout = t;

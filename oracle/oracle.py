@@ -82,6 +82,7 @@ def lib():
                 "orc_min_over_mean": (dbl, [i32, P(u64)]),
                 "orc_width": (i32, [i32, P(u64)]),
                 "orc_accessible_in_range": (i32, [i32, P(u64)]),
+                "orc_kl_support": (i32, [i32, i32, i32, P(u64)]),
                 "orc_kullback_leibler": (dbl, [i32, P(u64), dbl]),
                 "orc_chebyshev": (dbl, [i32, P(u64)]),
                 "orc_iterate": (i32, [i32, i64, u64, P(i8), P(i32), P(dbl), P(u64), P(Params),

@@ -12,8 +12,8 @@ ROOT = os.path.dirname(PKG)
 CSRC = os.path.join(PKG, "csrc")
 BUILD = os.path.join(PKG, "_build")
 LIB = os.path.join(PKG, "libmuca.so")
-SOURCES = ["muca_kernels.cu", "muca_api.cu"]
-HEADERS = ["muca_internal.h"]
+SOURCES = ["muca_kernels.cu", "muca_batch.cu", "muca_noalloc.cu", "muca_api.cu"] + [f"muca_full_{L}.cu" for L in (8, 16, 24, 32, 48, 64)]
+HEADERS = ["muca_internal.h", "muca_device.cuh", "muca_full.cuh"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 
@@ -55,7 +55,7 @@ def build(force: bool = False, verbose: bool = False, ptxas_info: bool = False) 
             sys.stderr.write(r.stdout + r.stderr)
         return obj
 
-    with ThreadPoolExecutor(max_workers=len(SOURCES)) as ex:
+    with ThreadPoolExecutor(max_workers=min(len(SOURCES), max(2, os.cpu_count() or 2))) as ex:
         objs = list(ex.map(compile_one, SOURCES))
     tmp = LIB + f".tmp{os.getpid()}"
     cmd = [cc] + ARCH + ["-shared", "-o", tmp] + objs

@@ -110,6 +110,7 @@ struct muca_s {
     cudaEvent_t table_copied = nullptr;    // last table upload has left h_table
     std::vector<double> lnW;
     uint64_t t = 0;                  // attempt counter (tag 0 stream)
+    int32_t kl_lo = -1, kl_hi = -1;  // range visited in the previous batched iteration
 };
 
 namespace {
@@ -263,6 +264,22 @@ bool visited_range(int32_t N, const std::vector<uint64_t> &H, int32_t &lo, int32
             hi = e;
         }
     return lo >= 0;
+}
+
+// KL reference size (the Eq. (6) reading): accessible energies in the union of the
+// previous iteration's range and the tested histogram's range, at least 10.
+int32_t kl_support(int32_t N, int32_t prev_lo, int32_t prev_hi, const std::vector<uint64_t> &H)
+{
+    int32_t lo = prev_lo, hi = prev_hi, clo, chi;
+    if (visited_range(N, H, clo, chi)) {
+        lo = lo < 0 ? clo : std::min(lo, clo);
+        hi = hi < 0 ? chi : std::max(hi, chi);
+    }
+    int32_t count = 0;
+    if (lo >= 0)
+        for (int32_t e = lo; e <= hi; ++e)
+            count += accessible(N, e) ? 1 : 0;
+    return std::max(count, 10);
 }
 
 int validate(muca_t h)
@@ -575,7 +592,7 @@ bool member_update(muca_t h, const muca_params &p, muca_stats &s)
     if (p.stop_rule == MUCA_STOP_MIN_MEAN)
         metric = min_over_mean(N, H);
     else if (p.stop_rule == MUCA_STOP_KL)
-        metric = kullback_leibler(N, H, (double)(N - 1));
+        metric = kullback_leibler(N, H, (double)kl_support(N, h->kl_lo, h->kl_hi, H));
     else
         metric = chebyshev(N, H);
     s.last_metric = metric;
@@ -587,6 +604,8 @@ bool member_update(muca_t h, const muca_params &p, muca_stats &s)
     for (int32_t e = 0; e <= N; ++e)
         if (H[(size_t)e])
             h->lnW[(size_t)e] -= std::log((double)H[(size_t)e]);
+    if (!visited_range(N, H, h->kl_lo, h->kl_hi))
+        h->kl_lo = h->kl_hi = -1;
     return s.iterations >= p.max_iterations;
 }
 
@@ -893,7 +912,7 @@ int muca_iterate_until_flat(muca_t h, const muca_params *p_in, muca_stats *stats
     const auto start = std::chrono::steady_clock::now();
     const int32_t N = h->N;
     std::vector<uint64_t> H;
-    int32_t prev_width = 0, prev_accessible = 0;
+    int32_t prev_width = 0, prev_lo = -1, prev_hi = -1;
     bool full = false;
     uint64_t upd_prev = 0, spent = 0;
     int32_t n = 0;
@@ -901,11 +920,9 @@ int muca_iterate_until_flat(muca_t h, const muca_params *p_in, muca_stats *stats
     double metric = 0.0;
     while (n < p.max_iterations) {
         uint64_t n_therm, n_upd;
-        double q;
         if (p.schedule == MUCA_SCHEDULE_SWEEPS) {
             n_therm = p.therm_sweeps * (uint64_t)N;
             n_upd = p.sweeps_per_iter * (uint64_t)N;
-            q = (double)(N - 1);
         } else {
             // Sec. 3: w = max(w', 10) with w' the extent covered in the previous
             // iteration; N_therm = f_therm w; Eq. (7) until the whole range was covered,
@@ -918,7 +935,6 @@ int muca_iterate_until_flat(muca_t h, const muca_params *p_in, muca_stats *stats
                 n_upd = (uint64_t)std::floor(p.factor * std::pow((double)w, p.z) / (double)h->W) + 1u;
                 full = prev_width == N + 1;
             }
-            q = (double)std::max(prev_accessible, 10);
         }
         rc = upload_table(h);
         if (rc)
@@ -940,7 +956,7 @@ int muca_iterate_until_flat(muca_t h, const muca_params *p_in, muca_stats *stats
         if (p.stop_rule == MUCA_STOP_MIN_MEAN)
             metric = min_over_mean(N, H);
         else if (p.stop_rule == MUCA_STOP_KL)
-            metric = kullback_leibler(N, H, q);
+            metric = kullback_leibler(N, H, (double)kl_support(N, prev_lo, prev_hi, H));
         else
             metric = chebyshev(N, H);
         flat = p.stop_rule == MUCA_STOP_MIN_MEAN ? metric >= p.flat_threshold : metric < p.flat_threshold;
@@ -953,11 +969,11 @@ int muca_iterate_until_flat(muca_t h, const muca_params *p_in, muca_stats *stats
         int32_t lo, hi;
         if (visited_range(N, H, lo, hi)) {
             prev_width = hi - lo + 1;
-            prev_accessible = 0;
-            for (int32_t e = lo; e <= hi; ++e)
-                prev_accessible += accessible(N, e) ? 1 : 0;
+            prev_lo = lo;
+            prev_hi = hi;
         } else {
-            prev_width = prev_accessible = 0;
+            prev_width = 0;
+            prev_lo = prev_hi = -1;
         }
         upd_prev = n_upd;
         if (p.deadline_s > 0.0) {
@@ -1282,6 +1298,8 @@ int muca_batch_iterate(muca_batch_t b, const muca_params *p_in, muca_stats *stat
     const auto start = std::chrono::steady_clock::now();
     std::vector<muca_stats> st(n);
     std::memset(st.data(), 0, sizeof(muca_stats) * n);
+    for (muca_t h : b->inst)
+        h->kl_lo = h->kl_hi = -1;
     std::vector<int32_t> active(n);
     for (size_t i = 0; i < n; ++i)
         active[i] = (int32_t)i;

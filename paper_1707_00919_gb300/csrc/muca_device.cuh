@@ -1,0 +1,571 @@
+// muca_device.cuh - device code of the whole-sweep kernels, shared by the per-L
+// translation units (muca_full_L.cu), the batched kernels (muca_batch.cu) and the
+// generic kernels (muca_kernels.cu).  Parallel multicanonical 2D Ising update of Gross,
+// Zierenberg, Weigel, Janke (arXiv:1707.00919), Sec. 2.3.
+#pragma once
+
+#include <cstddef>
+#include <cstdint>
+#include <type_traits>
+
+#include <cuda_runtime.h>
+
+#include "../../include/muca.h"
+#include "muca_internal.h"
+
+namespace muca {
+namespace {
+
+__host__ __device__ constexpr size_t align_up(size_t v, size_t a) { return (v + a - 1) / a * a; }
+
+template <typename RowT>
+__device__ __forceinline__ uint32_t bit_at(RowT w, int x)
+{
+    return (uint32_t)(w >> x) & 1u;
+}
+
+// ---------------------------------------------------------------------------------
+// Whole-sweep kernel, specialised on L.  A launch covers whole sweeps starting at a
+// sweep boundary.  Every row is unrolled, so bit positions and neighbour columns are
+// compile-time constants; the Philox round keys are computed once per thread.
+//
+// Row representation: the rows above (U), at (C) and below (D) the current row are held
+// as nibble words, eight spins per 32-bit register, one spin in bit 0 of each 4-bit
+// field (1 = spin down).  Field-parallel arithmetic gives for all sites of a row at once
+//   kb = [s != s_up] + [s != s_down] + [s != s_right]    h0 = [s != s_left]
+// with the original spins, so the antiparallel count of site x is k0 = kb + h0 if the
+// previous attempt (at x - 1) did not flip, else k1 = kb + 1 - h0.  Site 0's left
+// neighbour is site L-1 of the same row, not yet visited, so k1 = k0 there; site L-1's
+// right neighbour is site 0, so its counts move by one if site 0 flipped.
+//
+// Shared-memory table: one 28-byte row per energy index e, words 0..4 the acceptance
+// thresholds T[e][k], word 5 the block's histogram count of e, word 6 padding (a stride
+// of 7 words spreads the rows over all 32 banks; thermalization counts go there).  The energy is carried as the byte
+// address E of its row, so a threshold is at E + 4k, the histogram word at E + 20, and
+// an accepted flip moves E by 28 (2 - k).
+//
+// Latency: the threshold an attempt needs depends on whether the previous attempt
+// flipped (through E and through k).  Both candidates are loaded two attempts ahead and
+// the right one is picked once the previous decision is known, which takes the shared-
+// memory latency off the attempt-to-attempt dependency chain (select, compare).
+// ---------------------------------------------------------------------------------
+template <int L>
+struct RowOf {
+    using type = typename std::conditional<(L <= 32), uint32_t, unsigned long long>::type;
+};
+
+
+struct PhiloxKeys {
+    uint32_t k0[10], k1[10];   // round keys
+    uint32_t hi_w, lo_w;       // round-0 product of the walker counter word
+};
+
+__device__ __forceinline__ PhiloxKeys make_keys(uint64_t seed, uint32_t walker)
+{
+    PhiloxKeys p;
+#pragma unroll
+    for (int r = 0; r < 10; ++r) {
+        p.k0[r] = (uint32_t)seed + (uint32_t)r * 0x9E3779B9u;
+        p.k1[r] = (uint32_t)(seed >> 32) + (uint32_t)r * 0xBB67AE85u;
+    }
+    const unsigned long long pw = (unsigned long long)0xCD9E8D57u * walker;
+    p.hi_w = (uint32_t)(pw >> 32);
+    p.lo_w = (uint32_t)pw;
+    return p;
+}
+
+// Philox4x32-10 on counter (c0, c1, walker, tag 0) with precomputed keys; the products
+// are formed as 64-bit results so that one wide multiply gives both halves.
+__device__ __forceinline__ uint4 philox_walker(uint32_t c0, uint32_t c1, const PhiloxKeys &p)
+{
+    const unsigned long long q = (unsigned long long)0xD2511F53u * c0;
+    uint32_t x0 = p.hi_w ^ c1 ^ p.k0[0];
+    uint32_t x1 = p.lo_w;
+    uint32_t x2 = (uint32_t)(q >> 32) ^ p.k1[0];
+    uint32_t x3 = (uint32_t)q;
+#pragma unroll
+    for (int r = 1; r < 10; ++r) {
+        const unsigned long long p0 = (unsigned long long)0xD2511F53u * x0;
+        const unsigned long long p1 = (unsigned long long)0xCD9E8D57u * x2;
+        const uint32_t n0 = (uint32_t)(p1 >> 32) ^ x1 ^ p.k0[r];
+        const uint32_t n2 = (uint32_t)(p0 >> 32) ^ x3 ^ p.k1[r];
+        x0 = n0;
+        x1 = (uint32_t)p1;
+        x2 = n2;
+        x3 = (uint32_t)p0;
+    }
+    return make_uint4(x0, x1, x2, x3);
+}
+
+// 32x32 bit transpose across a warp: lane l holds m with bit j = A[l][j]; returns in
+// lane j the word with bit l = A[l][j].  Five butterfly stages of shuffles.
+__device__ __forceinline__ uint32_t warp_transpose32(uint32_t m, int lane)
+{
+    const uint32_t masks[5] = {0x0000FFFFu, 0x00FF00FFu, 0x0F0F0F0Fu, 0x33333333u, 0x55555555u};
+#pragma unroll
+    for (int i = 0; i < 5; ++i) {
+        const int s = 16 >> i;
+        const uint32_t part = __shfl_xor_sync(0xFFFFFFFFu, m, s);
+        m = (lane & s) ? ((m & ~masks[i]) | ((part >> s) & masks[i])) : ((m & masks[i]) | ((part & masks[i]) << s));
+    }
+    return m;
+}
+
+// Sign bits of four int8 spins (-1 = 0xFF, +1 = 0x01) as a nibble.
+__device__ __forceinline__ uint32_t gather_signs(uint32_t v) { return ((v & 0x80808080u) * 0x00204081u) >> 28; }
+
+// Nibble of down-spin bits to four int8 spins.
+__device__ __forceinline__ uint32_t spread_signs(uint32_t n)
+{
+    return 0x01010101u | (((n * 0x00204081u) & 0x01010101u) * 0xFEu);
+}
+
+// Bit rows of the warp's 32 walkers from the int8 [site][walker] layout, R rows at a
+// time so that their loads are in flight together; lane j receives walker w0 + j.
+// All 32 walkers must exist and W % 16 == 0.
+template <int L, int R, typename RowT>
+__device__ __forceinline__ void warp_load_rows_int8(const int8_t *g, int64_t W, int64_t w0, int y0, int lane,
+                                                    RowT (&out)[R])
+{
+    constexpr int HALVES = (L + 31) / 32;
+    uint4 a[R][HALVES], b[R][HALVES];
+#pragma unroll
+    for (int r = 0; r < R; ++r)
+#pragma unroll
+        for (int half = 0; half < HALVES; ++half) {
+            const int x = half * 32 + lane;
+            if (x < L) {
+                const uint4 *p = reinterpret_cast<const uint4 *>(g + (size_t)((y0 + r) * L + x) * (size_t)W + (size_t)w0);
+                a[r][half] = p[0];
+                b[r][half] = p[1];
+            } else {
+                a[r][half] = make_uint4(0, 0, 0, 0);
+                b[r][half] = make_uint4(0, 0, 0, 0);
+            }
+        }
+#pragma unroll
+    for (int r = 0; r < R; ++r) {
+        RowT row = 0;
+#pragma unroll
+        for (int half = 0; half < HALVES; ++half) {
+            const uint4 u = a[r][half], v = b[r][half];
+            uint32_t m = gather_signs(u.x) | (gather_signs(u.y) << 4) | (gather_signs(u.z) << 8) |
+                         (gather_signs(u.w) << 12) | (gather_signs(v.x) << 16) | (gather_signs(v.y) << 20) |
+                         (gather_signs(v.z) << 24) | (gather_signs(v.w) << 28);
+            m = warp_transpose32(m, lane);
+            row |= (RowT)m << (32 * half);
+        }
+        out[r] = row;
+    }
+}
+
+template <int L, typename RowT>
+__device__ __forceinline__ void warp_store_row_int8(int8_t *g, int64_t W, int64_t w0, int y, int lane, RowT r)
+{
+#pragma unroll
+    for (int half = 0; half < (L + 31) / 32; ++half) {
+        const uint32_t m = warp_transpose32((uint32_t)(r >> (32 * half)), lane);
+        const int x = half * 32 + lane;
+        if (x < L) {
+            uint4 *p = reinterpret_cast<uint4 *>(g + (size_t)(y * L + x) * (size_t)W + (size_t)w0);
+            p[0] = make_uint4(spread_signs(m & 15u), spread_signs((m >> 4) & 15u), spread_signs((m >> 8) & 15u),
+                              spread_signs((m >> 12) & 15u));
+            p[1] = make_uint4(spread_signs((m >> 16) & 15u), spread_signs((m >> 20) & 15u),
+                              spread_signs((m >> 24) & 15u), spread_signs(m >> 28));
+        }
+    }
+}
+
+// Eight bits -> eight nibbles (bit i to bit 4i), and back.
+__device__ __forceinline__ uint32_t spread8(uint32_t b)
+{
+    uint32_t x = b & 0xFFu;
+    x = (x | (x << 12)) & 0x000F000Fu;
+    x = (x | (x << 6)) & 0x03030303u;
+    x = (x | (x << 3)) & 0x11111111u;
+    return x;
+}
+
+__device__ __forceinline__ uint32_t pack8(uint32_t x)
+{
+    x &= 0x11111111u;
+    x = (x | (x >> 3)) & 0x03030303u;
+    x = (x | (x >> 6)) & 0x000F000Fu;
+    x = (x | (x >> 12)) & 0xFFu;
+    return x;
+}
+
+template <int L>
+__device__ __forceinline__ void to_nibbles(typename RowOf<L>::type r, uint32_t (&n)[L / 8])
+{
+#pragma unroll
+    for (int i = 0; i < L / 8; ++i)
+        n[i] = spread8((uint32_t)(r >> (8 * i)));
+}
+
+template <int L>
+__device__ __forceinline__ typename RowOf<L>::type from_nibbles(const uint32_t (&n)[L / 8])
+{
+    using RowT = typename RowOf<L>::type;
+    RowT r = 0;
+#pragma unroll
+    for (int i = 0; i < L / 8; ++i)
+        r |= (RowT)pack8(n[i]) << (8 * i);
+    return r;
+}
+
+// Row storage in shared memory during a launch.  L <= 32: nibble words,
+// [row][walker][L/8], read and written without conversion.  L > 32: bit words
+// [row][walker] (a nibble copy would not fit next to the table), converted per row.
+template <int L>
+struct SmemRows {
+    static constexpr bool kNibbles = (L <= 32);
+    static constexpr int NW = L / 8;
+    using RowT = typename RowOf<L>::type;
+    static constexpr size_t bytes_per_walker() { return kNibbles ? (size_t)L * NW * 4 : (size_t)L * sizeof(RowT); }
+
+    unsigned char *base;
+    int wpb, tid;
+
+    __device__ __forceinline__ void load(int y, uint32_t (&n)[NW]) const
+    {
+        if (kNibbles) {
+            const uint32_t *p = reinterpret_cast<const uint32_t *>(base) + ((size_t)y * wpb + tid) * NW;
+#pragma unroll
+            for (int i = 0; i < NW; ++i)
+                n[i] = p[i];
+        } else {
+            to_nibbles<L>(reinterpret_cast<const RowT *>(base)[(size_t)y * wpb + tid], n);
+        }
+    }
+    __device__ __forceinline__ void store(int y, const uint32_t (&n)[NW]) const
+    {
+        if (kNibbles) {
+            uint32_t *p = reinterpret_cast<uint32_t *>(base) + ((size_t)y * wpb + tid) * NW;
+#pragma unroll
+            for (int i = 0; i < NW; ++i)
+                p[i] = n[i];
+        } else {
+            reinterpret_cast<RowT *>(base)[(size_t)y * wpb + tid] = from_nibbles<L>(n);
+        }
+    }
+    __device__ __forceinline__ void store_bits(int y, RowT r) const
+    {
+        if (kNibbles) {
+            uint32_t n[NW];
+            to_nibbles<L>(r, n);
+            store(y, n);
+        } else {
+            reinterpret_cast<RowT *>(base)[(size_t)y * wpb + tid] = r;
+        }
+    }
+    __device__ __forceinline__ RowT load_bits(int y) const
+    {
+        if (kNibbles) {
+            uint32_t n[NW];
+            load(y, n);
+            return from_nibbles<L>(n);
+        }
+        return reinterpret_cast<const RowT *>(base)[(size_t)y * wpb + tid];
+    }
+};
+
+__device__ __forceinline__ uint32_t lds_u32(uint32_t addr)
+{
+    uint32_t v;
+    asm volatile("ld.shared.u32 %0, [%1];" : "=r"(v) : "r"(addr));
+    return v;
+}
+
+// Histogram record of one attempt: one count for the post-decision energy, added to the
+// histogram word (offset 20) of its table row.  A shared-memory reduction is issued on
+// every attempt anyway (a predicated one, which would allow run-length counting, measured
+// about 45 cycles slower per attempt), so a plain +1 needs no further arithmetic.
+__device__ __forceinline__ void hist_add_one(uint32_t E)
+{
+    asm volatile("red.shared.add.u32 [%0+20], 1;" :: "r"(E));
+}
+
+// Thermalization launches add the same count to the row's padding word (offset 24),
+// which nothing reads.  The reduction orders the shared-memory threshold loads of later
+// attempts behind it exactly as in a recording launch; without it the compiler's
+// schedule was measured 11% slower (72 vs 64 cycles per attempt and warp at L = 32).
+__device__ __forceinline__ void pad_add_one(uint32_t E)
+{
+    asm volatile("red.shared.add.u32 [%0+24], 1;" :: "r"(E));
+}
+
+// Byte offset 4k of the count field x (k in 0..4) of a nibble word.
+__device__ __forceinline__ uint32_t field_x4(uint32_t w, int f)
+{
+    return (f == 0 ? (w << 2) : (w >> (4 * f - 2))) & 0x1Cu;
+}
+
+// One row of L attempts (typewriter, x = 0 .. L-1) for one walker.  E is the shared
+// byte address of the current energy's table row on entry and on exit.
+// Random words of the current row: four attempts at a time, already clamped to
+// 0xFFFFFFFE so that "r < T" also accepts every attempt when T = 0xFFFFFFFF.
+struct PhiloxSource {
+    uint64_t blk;            // Philox block of column 0 of the row
+    const PhiloxKeys *pk;
+    __device__ __forceinline__ uint4 get(int xb) const
+    {
+        const uint64_t b = blk + (uint64_t)(xb / 4);
+        const uint4 rw = philox_walker((uint32_t)b, (uint32_t)(b >> 32), *pk);
+        return make_uint4(min(rw.x, 0xFFFFFFFEu), min(rw.y, 0xFFFFFFFEu), min(rw.z, 0xFFFFFFFEu),
+                          min(rw.w, 0xFFFFFFFEu));
+    }
+};
+
+// MASKED: only the attempts x in [x_begin, x_end) happen (a launch that starts or ends
+// inside the row); the others neither flip nor count, their random words go unused.
+template <int L, bool RECORD, bool MASKED, class Src>
+__device__ __forceinline__ void process_row(const uint32_t (&U)[L / 8], uint32_t (&C)[L / 8], const uint32_t (&D)[L / 8],
+                                            uint32_t &E, const Src &src, int x_begin = 0, int x_end = L)
+{
+    constexpr int NW = L / 8;
+    uint32_t K0[NW], K1[NW];
+#pragma unroll
+    for (int i = 0; i < NW; ++i) {
+        const uint32_t cr = __funnelshift_r(C[i], C[(i + 1) % NW], 4);        // field f <- right neighbour
+        const uint32_t cl = __funnelshift_l(C[(i + NW - 1) % NW], C[i], 4);   // field f <- left neighbour
+        const uint32_t kb = (U[i] ^ C[i]) + (D[i] ^ C[i]) + (C[i] ^ cr);
+        const uint32_t h0 = C[i] ^ cl;
+        K0[i] = kb + h0;
+        K1[i] = kb + 0x11111111u - h0;
+    }
+    // site L-1: its right neighbour is site 0, whose flip moves the count by -1 if the
+    // two disagreed before, +1 if they agreed (in units of 4 bytes here)
+    const uint32_t hr_last = ((C[NW - 1] >> 28) ^ C[0]) & 1u;
+    const uint32_t adj_if_flip = hr_last ? (uint32_t)-4 : 4u;
+    uint32_t adj_last = 0u;
+
+#define MUCA_SITE_J(x, J0v, J1v)                                                         \
+    do {                                                                                 \
+        J0v = field_x4(K0[(x) >> 3], (x) & 7);                                           \
+        J1v = ((x) == 0) ? J0v : field_x4(K1[(x) >> 3], (x) & 7);                        \
+        if ((x) == L - 1) {                                                              \
+            J0v += adj_last;                                                             \
+            J1v += adj_last;                                                             \
+        }                                                                                \
+    } while (0)
+
+    // attempt 0 (E resolved) and both outcomes of it for attempt 1
+    uint32_t J0a, J1a, J0b, J1b;
+    MUCA_SITE_J(0, J0a, J1a);
+    MUCA_SITE_J(1, J0b, J1b);
+    uint32_t d0_cur = 56u - 7u * J0a, d1_cur = d0_cur;               // attempt x
+    uint32_t d0_next = 56u - 7u * J0b, d1_next = 56u - 7u * J1b;     // attempt x + 1
+    uint32_t T0n = lds_u32(E + J0a), T1n = T0n;                      // candidates of x
+    uint32_t T0nn = lds_u32(E + J0b), T1nn = lds_u32(E + d0_cur + J1b);   // of x + 1
+    bool prev_acc = false;
+    uint32_t Eres = E;
+
+#pragma unroll
+    for (int xb = 0; xb < L; xb += 4) {
+        const uint4 rw = src.get(xb);
+        const uint32_t words[4] = {rw.x, rw.y, rw.z, rw.w};
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+            const int x = xb + u;
+            // decision of attempt x
+            const uint32_t T = prev_acc ? T1n : T0n;
+            const uint32_t dsel = prev_acc ? d1_cur : d0_cur;
+            const bool in_range = !MASKED || (x >= x_begin && x < x_end);
+            const bool acc = (words[u] < T) && in_range;
+            const uint32_t Epost = acc ? Eres + dsel : Eres;
+            C[x >> 3] ^= acc ? (1u << (4 * (x & 7))) : 0u;
+            if (x == 0)
+                adj_last = acc ? adj_if_flip : 0u;
+            if (RECORD && in_range)
+                hist_add_one(Epost);
+            else
+                pad_add_one(Epost);
+            // candidates of attempt x + 2 for both outcomes of attempt x + 1
+            T0n = T0nn;
+            T1n = T1nn;
+            if (x + 2 < L) {
+                uint32_t J0c, J1c;
+                MUCA_SITE_J(x + 2, J0c, J1c);
+                const uint32_t dnext = acc ? d1_next : d0_next;      // energy step of x + 1 if accepted
+                T0nn = lds_u32(Epost + J0c);
+                T1nn = lds_u32(Epost + dnext + J1c);
+                d0_cur = d0_next;
+                d1_cur = d1_next;
+                d0_next = 56u - 7u * J0c;
+                d1_next = 56u - 7u * J1c;
+            } else if (x + 1 < L) {
+                d0_cur = d0_next;
+                d1_cur = d1_next;
+            }
+            Eres = Epost;
+            prev_acc = acc;
+        }
+    }
+#undef MUCA_SITE_J
+    E = Eres;
+}
+
+// One block's share of a launch: walkers wbase .. wbase + wpb - 1 of the instance in
+// `a` (threads tid >= wpb idle), all of the launch's whole sweeps.  Shared memory:
+// the table, then the rows of the wpb walkers.  Every thread of the block calls it.
+// The layout only changes the loads and stores around the sweeps; callers with a
+// compile-time layout get it folded, the batched kernels pass it at run time.
+template <int L, bool RECORD, bool PARTIAL = false>
+__device__ __forceinline__ void sweep_block(const SweepArgs &a, int64_t wbase, int wpb, unsigned char *smem,
+                                            const int LAYOUT)
+{
+    using RowT = typename RowOf<L>::type;
+    constexpr int N = L * L;
+    constexpr int NB = N + 1;
+    constexpr int NW = L / 8;
+    constexpr int RB = 4;   // rows per batch of int8 loads
+    const int nthr = blockDim.x;
+    uint32_t *sTab = reinterpret_cast<uint32_t *>(smem);
+    const int tid = threadIdx.x;
+    const SmemRows<L> rows{smem + align_up((size_t)NB * kTableStride * 4, 16), wpb, tid};
+    const int lane = tid & 31;
+    const bool in_item = tid < wpb;
+    const int64_t w = wbase + tid;
+    const int64_t w0 = w - lane;
+    bool active = in_item && w < a.W;
+    const bool warp_full = in_item && (w0 + 32 <= a.W) && (a.W % 16 == 0);
+
+    for (int i = tid; i < NB * kTableStride; i += nthr) {
+        const int e = i / kTableStride, k = i - e * kTableStride;
+        sTab[i] = k < 5 ? a.table[e * 5 + k] : 0u;
+    }
+
+    if (LAYOUT == MUCA_LAYOUT_PACKED) {
+        if (active)
+            for (int y = 0; y < L; ++y)
+                rows.store_bits(y, reinterpret_cast<const RowT *>(a.lattice)[(size_t)y * a.W + w]);
+    } else if (warp_full) {
+        for (int y = 0; y < L; y += RB) {
+            RowT r[RB];
+            warp_load_rows_int8<L, RB, RowT>(reinterpret_cast<const int8_t *>(a.lattice), a.W, w0, y, lane, r);
+#pragma unroll
+            for (int i = 0; i < RB; ++i)
+                rows.store_bits(y + i, r[i]);
+        }
+    } else if (active) {
+        const int8_t *g = reinterpret_cast<const int8_t *>(a.lattice);
+        for (int y = 0; y < L; ++y) {
+            RowT r = 0;
+            for (int x = 0; x < L; ++x)
+                r |= (RowT)(g[(size_t)(y * L + x) * a.W + w] < 0) << x;
+            rows.store_bits(y, r);
+        }
+    }
+    int32_t e = 0;
+    if (active) {
+        e = a.energy[w];
+        if (e < 0 || e > N) {
+            atomicOr(a.err, kErrEnergyRange);
+            active = false;
+        }
+    }
+    __syncthreads();
+
+    if (active) {
+        const PhiloxKeys pk = make_keys(a.seed, (uint32_t)w);
+        const uint32_t tbase = (uint32_t)__cvta_generic_to_shared(sTab);
+        uint32_t U[NW], C[NW], D[NW];
+        uint32_t E = tbase + (uint32_t)e * (4u * kTableStride);
+        if (!PARTIAL) {
+            // whole sweeps from a sweep boundary
+            uint64_t blk = a.t0 >> 2;
+            const uint64_t nsweeps = a.n / (uint64_t)N;
+            rows.load(L - 1, U);
+            rows.load(0, C);
+            rows.load(1, D);
+            for (uint64_t s = 0; s < nsweeps; ++s) {
+#pragma unroll 1
+                for (int y = 0; y < L; ++y) {
+                    const PhiloxSource src{blk, &pk};
+                    process_row<L, RECORD, false>(U, C, D, E, src);
+                    rows.store(y, C);
+                    const int y2 = (y + 2 < L) ? y + 2 : y + 2 - L;
+#pragma unroll
+                    for (int i = 0; i < NW; ++i) {
+                        U[i] = C[i];
+                        C[i] = D[i];
+                    }
+                    rows.load(y2, D);
+                    blk += (uint64_t)(L / 4);
+                }
+            }
+        } else {
+            // any attempt range: rows cut by the launch's start or end run masked
+            uint64_t t = a.t0;
+            const uint64_t tend = a.t0 + a.n;
+            int y = (int)((t % (uint64_t)N) / L);
+            int x0 = (int)((t % (uint64_t)N) % L);
+            uint64_t blk = (t - (uint64_t)x0) >> 2;   // Philox block of column 0 of row y
+            rows.load((y + L - 1) % L, U);
+            rows.load(y, C);
+            rows.load((y + 1) % L, D);
+            while (t < tend) {
+                const uint64_t left = tend - t;
+                const PhiloxSource src{blk, &pk};
+                int xe = L;
+                if (x0 == 0 && left >= (uint64_t)L) {
+                    process_row<L, RECORD, false>(U, C, D, E, src);
+                } else {
+                    xe = left < (uint64_t)(L - x0) ? x0 + (int)left : L;
+                    process_row<L, RECORD, true>(U, C, D, E, src, x0, xe);
+                }
+                rows.store(y, C);
+                t += (uint64_t)(xe - x0);
+                if (xe < L)
+                    break;   // the launch ends inside this row
+                const int y2 = (y + 2 < L) ? y + 2 : y + 2 - L;
+#pragma unroll
+                for (int i = 0; i < NW; ++i) {
+                    U[i] = C[i];
+                    C[i] = D[i];
+                }
+                rows.load(y2, D);
+                y = (y + 1 == L) ? 0 : y + 1;
+                x0 = 0;
+                blk += (uint64_t)(L / 4);
+            }
+        }
+        e = (int32_t)((E - tbase) / (4u * kTableStride));
+    }
+    __syncthreads();
+    if (RECORD)
+        for (int i = tid; i < NB; i += nthr) {
+            const uint32_t v = sTab[i * kTableStride + kHistSlot];
+            if (v)
+                atomicAdd(&a.hist[i], (unsigned long long)v);
+        }
+    if (LAYOUT == MUCA_LAYOUT_PACKED) {
+        if (active)
+            for (int y = 0; y < L; ++y)
+                reinterpret_cast<RowT *>(a.lattice)[(size_t)y * a.W + w] = rows.load_bits(y);
+    } else if (warp_full) {
+        // a walker flagged invalid above kept its lattice in shared memory unchanged
+        for (int y = 0; y < L; ++y)
+            warp_store_row_int8<L, RowT>(reinterpret_cast<int8_t *>(a.lattice), a.W, w0, y, lane, rows.load_bits(y));
+    } else if (active) {
+        int8_t *g = reinterpret_cast<int8_t *>(a.lattice);
+        for (int y = 0; y < L; ++y) {
+            const RowT r = rows.load_bits(y);
+            for (int x = 0; x < L; ++x)
+                g[(size_t)(y * L + x) * a.W + w] = bit_at(r, x) ? (int8_t)-1 : (int8_t)1;
+        }
+    }
+    if (active)
+        a.energy[w] = e;
+}
+
+// A batched work item: the whole-sweep body of the item's instance.
+template <int L, bool RECORD>
+__device__ __forceinline__ void batch_item(const SweepArgs &a, const BatchItem &it, unsigned char *smem)
+{
+    sweep_block<L, RECORD>(a, it.wbase, it.wpb, smem, a.layout);
+}
+
+}  // namespace
+}  // namespace muca

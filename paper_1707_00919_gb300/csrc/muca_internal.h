@@ -9,6 +9,11 @@
 
 namespace muca {
 
+// Shared-memory table of the whole-sweep kernels: one row of kTableStride words per
+// energy, thresholds in words 0..4, the block's histogram count in word kHistSlot.
+constexpr int kTableStride = 7;
+constexpr int kHistSlot = 5;
+
 // Device error word bits.
 constexpr uint32_t kErrEnergyRange = 1u;   // a walker's energy index was off the grid
 constexpr uint32_t kErrSyncTimeout = 2u;   // a bounded wait inside a kernel gave up
@@ -45,9 +50,9 @@ size_t full_smem_bytes(int L, int walkers_per_block, bool record);
 // Largest dynamic shared memory a block may use on this device (bytes).
 size_t sweep_smem_limit();
 
-// Runs attempts [t0, t0 + n) of every walker: whole sweeps go to the kernel specialised
-// for L (L in {8, 16, 24, 32, 48, 64}), partial sweeps and other L to the generic kernel.
-// Grid = ceil(W / walkers_per_block) per launch.
+// Runs attempts [t0, t0 + n) of every walker in one launch: the kernel specialised for
+// L (L in {8, 16, 24, 32, 48, 64}; whole sweeps or, with its partial-row path, any
+// range), the generic kernel for other L.  Grid = ceil(W / walkers_per_block).
 cudaError_t launch_sweep(const SweepArgs &a, int walkers_per_block, bool record, cudaStream_t s);
 
 // Routes whole sweeps to the generic kernel when false (used by tests that compare the
@@ -65,6 +70,21 @@ cudaError_t launch_unpack(int32_t L, int32_t layout, int64_t W, const void *latt
 // Evaluates the device Philox4x32-10 on n counters.
 cudaError_t launch_philox(const uint32_t *ctr, uint32_t k0, uint32_t k1, size_t n, uint32_t *out,
                           cudaStream_t s);
+
+// Kernels of one L each (muca_full_L.cu): launch over any attempt range, and resident
+// blocks of the recording kernel per SM.
+cudaError_t launch_full_L8(const SweepArgs &a, int wpb, bool record, cudaStream_t s);
+cudaError_t launch_full_L16(const SweepArgs &a, int wpb, bool record, cudaStream_t s);
+cudaError_t launch_full_L24(const SweepArgs &a, int wpb, bool record, cudaStream_t s);
+cudaError_t launch_full_L32(const SweepArgs &a, int wpb, bool record, cudaStream_t s);
+cudaError_t launch_full_L48(const SweepArgs &a, int wpb, bool record, cudaStream_t s);
+cudaError_t launch_full_L64(const SweepArgs &a, int wpb, bool record, cudaStream_t s);
+int occupancy_full_L8(int layout, int wpb);
+int occupancy_full_L16(int layout, int wpb);
+int occupancy_full_L24(int layout, int wpb);
+int occupancy_full_L32(int layout, int wpb);
+int occupancy_full_L48(int layout, int wpb);
+int occupancy_full_L64(int layout, int wpb);
 
 // Blocks of the recording sweep kernel for this L, layout and block size that one SM
 // holds at once (0 if the configuration does not fit).

@@ -106,14 +106,15 @@ def test_sweeps_bit_exact(muca_mod, orc, layout, L, W, wpb):
 
 
 @pytest.mark.parametrize("layout", [0, 1])
-def test_partial_sweeps_bit_exact(muca_mod, orc, layout):
+@pytest.mark.parametrize("L", [8, 12, 32, 64])
+def test_partial_sweeps_bit_exact(muca_mod, orc, layout, L):
     """Launch boundaries inside rows and inside Philox blocks (Eq. 7 asks for attempt
-    counts that are not whole sweeps)."""
-    L, W = 8, 77
+    counts that are not whole sweeps); L = 12 runs the generic kernel."""
+    W = 77
     N = L * L
-    lnW = rand_weights(L, 1)
+    lnW = rand_weights(L, 1, 0.4 if L <= 12 else 0.05)
     plan = [(5, False, True), (1, True, True), (70, True, False), (3, True, False), (N * 2 + 9, True, False),
-            (13, False, False), (N - 1, True, False)]
+            (13, False, False), (N - 1, True, False), (L + 2, True, False), (3 * L - 1, False, False)]
     (lat, e, H, t), (s, eo, Ho, to) = run_both(muca_mod, orc, L, W, 5, layout, 32, lnW, plan)
     assert t == to
     assert np.array_equal(lat, s) and np.array_equal(e, eo) and np.array_equal(H, Ho)
