@@ -144,14 +144,19 @@ class ClockSampler:
         return {"sm_mhz": sm[len(sm) // 2], "sm_max_mhz": mx, "reasons": sorted(reasons), "samples": len(sm)}
 
 
-KERNEL_SOURCE = os.path.join(ROOT, "paper_1707_00919_gb300", "csrc", "muca_kernels.cu")
+# Sources that define the timed whole-sweep kernel at L = 32 (body, launcher, constants).
+KERNEL_SOURCES = [os.path.join(ROOT, "paper_1707_00919_gb300", "csrc", f)
+                  for f in ("muca_device.cuh", "muca_full.cuh", "muca_full_32.cu", "muca_internal.h")]
 TRAFFIC_PROFILE = os.path.join(ROOT, "profiles", "sweep_full_kernel_L32_W16384_int8.md")
 
 
 def kernel_source_hash() -> str:
     import hashlib
-    with open(KERNEL_SOURCE, "rb") as f:
-        return hashlib.sha256(f.read()).hexdigest()[:16]
+    h = hashlib.sha256()
+    for path in KERNEL_SOURCES:
+        with open(path, "rb") as f:
+            h.update(f.read())
+    return h.hexdigest()[:16]
 
 
 def profiled_traffic():
