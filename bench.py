@@ -54,6 +54,41 @@ def config_dict():
             "l2": "flushed between timed steps (256 MiB write)", "parallelism": "independent instance per GPU"}
 
 
+def exact_ln_dos(L: int):
+    """ln g(e) of the periodic L x L lattice from the committed table (exact closed form,
+    tests/golden/exact_dos_L{L}.txt); -inf at the two inaccessible energies."""
+    import numpy as np
+    vals = []
+    with open(os.path.join(ROOT, "tests", "golden", f"exact_dos_L{L}.txt")) as f:
+        for line in f:
+            if not line.startswith("#"):
+                vals.append(float(line.split()[1]))
+    return np.array(vals, dtype=np.float64)
+
+
+def perfect_weights(L: int):
+    """ln W = -ln g (the perfect multicanonical weights of Sec. 3.1), 0 where g = 0."""
+    import numpy as np
+    lng = exact_ln_dos(L)
+    return np.where(np.isfinite(lng), -lng, 0.0)
+
+
+def time_recorded_sweeps(m, stream, sweeps: int, reps: int) -> float:
+    """Median device time (s) of `sweeps` recorded sweeps on the instance's stream."""
+    import torch
+    ts = []
+    for _ in range(reps):
+        a = torch.cuda.Event(enable_timing=True)
+        b = torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        m.sweep(sweeps, record=True)
+        b.record(stream)
+        stream.synchronize()
+        ts.append(a.elapsed_time(b) / 1e3)
+    ts.sort()
+    return ts[len(ts) // 2]
+
+
 # ----------------------------------------------------------------------------------
 # distributed plumbing
 # ----------------------------------------------------------------------------------
@@ -359,6 +394,17 @@ def run_native(args):
         "clocks": clocks.summary(),
     }
     m.close()
+
+    # ---- the paper's hardware protocol (Sec. 3.1): perfect weights, equilibrated ----
+    mp_ = M.Muca(L_SIDE, WALKERS, seed, layout=M.MUCA_LAYOUT_INT8, stream=stream)
+    mp_.set_weights(perfect_weights(L_SIDE))
+    mp_.sweep(THERM_SWEEPS, record=False)
+    pp_s = time_recorded_sweeps(mp_, stream, SWEEPS_PER_ITER, 7)
+    mp_.close()
+    pp_rate = WALKERS * SWEEPS_PER_ITER * N / pp_s
+    result["paper_protocol"] = {"attempts_per_s": pp_rate, "ns_per_flip": 1e9 / pp_rate,
+                                "protocol": f"ln W = -ln g exact, {THERM_SWEEPS} sweeps to equilibrate, "
+                                            f"median of 7 launches of {SWEEPS_PER_ITER} recorded sweeps"}
     if rank == 0 and not args.no_cpu_baseline:
         rate, cores, wall = cpu_baseline(lnW, WALKERS)
         result["cpu_baseline"] = {"value": rate, "unit": "attempts/s", "cores": cores, "kind": "oracle",
@@ -550,6 +596,48 @@ def run_serve_workload(args):
         "data": "synthetic"}))
 
 
+def run_fliptime_workload(args):
+    """Time per attempted flip against the walker count (the Fig. 2 protocol of Sec. 3.1:
+    perfect weights, timed after equilibration) for L = 16, 32, 64, up to twice the
+    full-occupancy count in steps of one block of 128 walkers (a multiple of it where
+    that would exceed 400 points), one instance per point."""
+    import numpy as np
+    import torch
+    import __graft_entry__
+    __graft_entry__.build()
+    from paper_1707_00919_gb300 import muca as M
+    dev = torch.cuda.current_device()
+    stream = torch.cuda.Stream()
+    out = {}
+    with ClockSampler(dev) as clocks:
+        for L in (16, 32, 64):
+            N = L * L
+            lnW = perfect_weights(L)
+            n_opt, wpb_opt = M.muca_optimal_walkers(L)
+            step = 128 * max(1, math.ceil(2 * n_opt / (128 * 400)))
+            sweeps = max(1, 10240 // N)
+            Ws, ns = [], []
+            for W in sorted(set(range(step, 2 * n_opt + 1, step)) | {n_opt}):
+                with M.Muca(L, W, SEED, stream=stream) as m:
+                    m.set_weights(lnW)
+                    m.sweep(3, record=False)
+                    t = time_recorded_sweeps(m, stream, sweeps, 3)
+                Ws.append(W)
+                ns.append(t * 1e9 / (W * sweeps * N))
+            best = int(np.argmin(ns))
+            out[f"L{L}"] = {"walkers": Ws, "ns_per_flip": [round(v, 6) for v in ns],
+                            "full_occupancy_walkers": n_opt, "full_occupancy_walkers_per_block": wpb_opt,
+                            "ns_per_flip_at_full_occupancy": ns[Ws.index(n_opt)] if n_opt in Ws else None,
+                            "best_walkers": Ws[best], "best_ns_per_flip": ns[best],
+                            "recorded_sweeps_per_point": sweeps, "step_walkers": step}
+    print(json.dumps({
+        "metric": "time per attempted spin flip vs walkers (perfect weights, after equilibration)",
+        "value": out["L32"]["best_ns_per_flip"], "unit": "ns/flip", "higher_is_better": False, "n_gpus": 1,
+        "scan": out, "clocks": clocks.summary(), "data": "synthetic: random +/-1 start, exact ln g weights",
+        "config": {"workload": "fliptime_scan_L16_L32_L64",
+                   "layout": "int8 [site][walker]", "walkers_per_block": "occupancy rule"}}))
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -557,7 +645,7 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["native", "reference"], default="native")
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--workload", choices=["headline", "batch", "serve"], default="headline")
+    ap.add_argument("--workload", choices=["headline", "batch", "serve", "fliptime"], default="headline")
     ap.add_argument("--serve-seconds", type=float, default=2.0)
     args = ap.parse_args()
     if args.workload == "batch":
@@ -565,6 +653,9 @@ def main():
         return
     if args.workload == "serve":
         run_serve_workload(args)
+        return
+    if args.workload == "fliptime":
+        run_fliptime_workload(args)
         return
     if args.warmup < 3 and args.impl == "native":
         args.warmup = 3

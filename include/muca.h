@@ -73,6 +73,10 @@ extern "C" {
  * one from the kernel's occupancy without timing. */
 #define MUCA_WPB_TUNE (-1)
 
+/* n_walkers value of muca_create / muca_create_ex that asks for the walker count of
+ * muca_optimal_walkers (the paper's default when W is not given, Sec. 3.1). */
+#define MUCA_WALKERS_OPTIMAL (-1)
+
 /* Stop rules of the weight iteration. */
 #define MUCA_STOP_MIN_MEAN 0     /* min H / mean H over accessible energies >= threshold    */
 #define MUCA_STOP_KL 1           /* Kullback-Leibler d_k < threshold (Eq. 6)                */
@@ -88,7 +92,7 @@ typedef struct muca_s *muca_t;
  * defaults (layout MUCA_LAYOUT_INT8, walkers_per_block chosen from the occupancy). */
 typedef struct {
     int32_t L;                   /* lattice side: multiple of 4, 4 <= L <= 64               */
-    int64_t n_walkers;           /* 1 <= n_walkers <= 2^31 - 1                              */
+    int64_t n_walkers;           /* 1 <= n_walkers <= 2^31 - 1, or MUCA_WALKERS_OPTIMAL     */
     uint64_t seed;               /* Philox key                                              */
     int32_t layout;              /* MUCA_LAYOUT_* (AUTO: measured choice)                   */
     int32_t walkers_per_block;   /* 0 = from occupancy, MUCA_WPB_TUNE = measured, else a
@@ -132,6 +136,17 @@ int muca_default_params(muca_params *p);
  * out == NULL), MUCA_ENOMEM, MUCA_ECUDA. */
 int muca_create(int32_t L, int64_t n_walkers, uint64_t seed, muca_t *out);
 int muca_create_ex(const muca_options *opt, muca_t *out);
+
+/* Walker count of full occupancy (Sec. 3.1: the first minimum of the time per attempted
+ * flip lies where every multiprocessor holds its maximal number of resident blocks, and
+ * the program uses that count when W is not given).  For lattice side L and layout
+ * (MUCA_LAYOUT_INT8 or MUCA_LAYOUT_PACKED) on the current device: the block size whose
+ * resident blocks per SM (whole-sweep kernel, shared memory and registers) hold the
+ * most walkers, ties to the larger block; *n_walkers = SMs x resident blocks x block
+ * size, *walkers_per_block (may be NULL) = that block size.  Nothing is allocated.
+ * Errors: MUCA_EINVAL (L as in muca_create, other layout, n_walkers NULL, no block size
+ * fits), MUCA_ECUDA. */
+int muca_optimal_walkers(int32_t L, int32_t layout, int64_t *n_walkers, int32_t *walkers_per_block);
 
 /* Frees all device and host memory of the instance (NULL is accepted). */
 int muca_destroy(muca_t h);

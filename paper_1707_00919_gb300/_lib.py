@@ -24,6 +24,7 @@ MUCA_LAYOUT_INT8 = 0
 MUCA_LAYOUT_PACKED = 1
 MUCA_LAYOUT_AUTO = 2
 MUCA_WPB_TUNE = -1
+MUCA_WALKERS_OPTIMAL = -1
 
 MUCA_STOP_MIN_MEAN = 0
 MUCA_STOP_KL = 1
@@ -87,6 +88,7 @@ SIGNATURES = {
     "muca_default_params": (ctypes.c_int, [_P(muca_params)]),
     "muca_create": (ctypes.c_int, [ctypes.c_int32, ctypes.c_int64, ctypes.c_uint64, _P(_H)]),
     "muca_create_ex": (ctypes.c_int, [_P(muca_options), _P(_H)]),
+    "muca_optimal_walkers": (ctypes.c_int, [ctypes.c_int32, ctypes.c_int32, _P(ctypes.c_int64), _P(ctypes.c_int32)]),
     "muca_destroy": (ctypes.c_int, [_H]),
     "muca_set_stream": (ctypes.c_int, [_H, ctypes.c_void_p]),
     "muca_set_allocator": (ctypes.c_int, [ALLOC_FN, RELEASE_FN, ctypes.c_void_p]),

@@ -682,6 +682,40 @@ int muca_create(int32_t L, int64_t n_walkers, uint64_t seed, muca_t *out)
     return muca_create_ex(&o, out);
 }
 
+int muca_optimal_walkers(int32_t L, int32_t layout, int64_t *n_walkers, int32_t *walkers_per_block)
+{
+    if (!n_walkers)
+        return fail(MUCA_EINVAL, "NULL argument");
+    if (L < 4 || L > 64 || L % 4 != 0)
+        return fail(MUCA_EINVAL, "L = %d: must be a multiple of 4 in [4, 64]", L);
+    if (layout != MUCA_LAYOUT_INT8 && layout != MUCA_LAYOUT_PACKED)
+        return fail(MUCA_EINVAL, "layout %d: must be MUCA_LAYOUT_INT8 or MUCA_LAYOUT_PACKED", layout);
+    int dev = 0, sms = 0;
+    cudaError_t err = cudaGetDevice(&dev);
+    if (err == cudaSuccess)
+        err = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    if (err != cudaSuccess)
+        return cuda_fail(err, "device query");
+    const size_t limit = muca::sweep_smem_limit();
+    int64_t best = 0;
+    int32_t best_wpb = 0;
+    for (int wpb = 32; wpb <= 256; wpb += 32) {
+        if (std::max(muca::sweep_smem_bytes(L, wpb, true), muca::full_smem_bytes(L, wpb, true)) > limit)
+            continue;
+        const int64_t per_sm = (int64_t)muca::resident_blocks(L, layout, wpb) * wpb;
+        if (per_sm > best || (per_sm == best && per_sm > 0)) {
+            best = per_sm;
+            best_wpb = wpb;
+        }
+    }
+    if (best == 0)
+        return fail(MUCA_EINVAL, "no block size fits L = %d", L);
+    *n_walkers = best * sms;
+    if (walkers_per_block)
+        *walkers_per_block = best_wpb;
+    return MUCA_OK;
+}
+
 int muca_create_ex(const muca_options *opt, muca_t *out)
 {
     if (!opt || !out)
@@ -690,6 +724,17 @@ int muca_create_ex(const muca_options *opt, muca_t *out)
     const int32_t L = opt->L;
     if (L < 4 || L > 64 || L % 4 != 0)
         return fail(MUCA_EINVAL, "L = %d: must be a multiple of 4 in [4, 64]", L);
+    if (opt->n_walkers == MUCA_WALKERS_OPTIMAL) {
+        muca_options o = *opt;
+        int32_t wpb = 0;
+        const int rc = muca_optimal_walkers(L, opt->layout == MUCA_LAYOUT_PACKED ? MUCA_LAYOUT_PACKED : MUCA_LAYOUT_INT8,
+                                            &o.n_walkers, &wpb);
+        if (rc != MUCA_OK)
+            return rc;
+        if (o.walkers_per_block == 0)
+            o.walkers_per_block = wpb;
+        return muca_create_ex(&o, out);
+    }
     if (opt->n_walkers < 1 || opt->n_walkers > INT32_MAX)
         return fail(MUCA_EINVAL, "n_walkers = %lld out of range", (long long)opt->n_walkers);
     if (opt->layout != MUCA_LAYOUT_INT8 && opt->layout != MUCA_LAYOUT_PACKED && opt->layout != MUCA_LAYOUT_AUTO)

@@ -47,7 +47,10 @@ __device__ __forceinline__ uint32_t bit_at(RowT w, int x)
 // Latency: the threshold an attempt needs depends on whether the previous attempt
 // flipped (through E and through k).  Both candidates are loaded two attempts ahead and
 // the right one is picked once the previous decision is known, which takes the shared-
-// memory latency off the attempt-to-attempt dependency chain (select, compare).
+// memory latency off the attempt-to-attempt dependency chain.  Both candidates are
+// compared with the random word as soon as they arrive, so the decision itself is one
+// select of two booleans, and both load addresses of the next-but-one attempt are
+// formed before the decision and selected by it.
 // ---------------------------------------------------------------------------------
 template <int L>
 struct RowOf {
@@ -369,11 +372,12 @@ __device__ __forceinline__ void process_row(const uint32_t (&U)[L / 8], uint32_t
         for (int u = 0; u < 4; ++u) {
             const int x = xb + u;
             // decision of attempt x
-            const uint32_t T = prev_acc ? T1n : T0n;
             const uint32_t dsel = prev_acc ? d1_cur : d0_cur;
+            const uint32_t Eacc = Eres + dsel;
+            const bool c0 = words[u] < T0n, c1 = words[u] < T1n;
             const bool in_range = !MASKED || (x >= x_begin && x < x_end);
-            const bool acc = (words[u] < T) && in_range;
-            const uint32_t Epost = acc ? Eres + dsel : Eres;
+            const bool acc = (prev_acc ? c1 : c0) && in_range;
+            const uint32_t Epost = acc ? Eacc : Eres;
             C[x >> 3] ^= acc ? (1u << (4 * (x & 7))) : 0u;
             if (x == 0)
                 adj_last = acc ? adj_if_flip : 0u;
@@ -387,9 +391,10 @@ __device__ __forceinline__ void process_row(const uint32_t (&U)[L / 8], uint32_t
             if (x + 2 < L) {
                 uint32_t J0c, J1c;
                 MUCA_SITE_J(x + 2, J0c, J1c);
-                const uint32_t dnext = acc ? d1_next : d0_next;      // energy step of x + 1 if accepted
-                T0nn = lds_u32(Epost + J0c);
-                T1nn = lds_u32(Epost + dnext + J1c);
+                const uint32_t a0 = acc ? Eacc + J0c : Eres + J0c;
+                const uint32_t a1 = acc ? Eacc + d1_next + J1c : Eres + d0_next + J1c;
+                T0nn = lds_u32(a0);
+                T1nn = lds_u32(a1);
                 d0_cur = d0_next;
                 d1_cur = d1_next;
                 d0_next = 56u - 7u * J0c;

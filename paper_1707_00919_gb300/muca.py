@@ -14,7 +14,7 @@ import numpy as np
 
 from . import _lib as C
 from ._lib import (MUCA_LAYOUT_AUTO, MUCA_LAYOUT_INT8, MUCA_LAYOUT_PACKED, MUCA_OK,  # noqa: F401
-                   MUCA_SCHEDULE_PAPER, MUCA_WPB_TUNE,
+                   MUCA_SCHEDULE_PAPER, MUCA_WALKERS_OPTIMAL, MUCA_WPB_TUNE,
                    MUCA_SCHEDULE_SWEEPS, MUCA_STOP_CHEBYSHEV, MUCA_STOP_KL, MUCA_STOP_MIN_MEAN,
                    muca_options, muca_params, muca_stats)
 
@@ -89,6 +89,14 @@ def muca_create_ex(L: int, n_walkers: int, seed: int, layout: int = MUCA_LAYOUT_
     h = ctypes.c_void_p()
     _check(C.load().muca_create_ex(ctypes.byref(o), ctypes.byref(h)))
     return h
+
+
+def muca_optimal_walkers(L: int, layout: int = MUCA_LAYOUT_INT8) -> tuple[int, int]:
+    """(walker count of full occupancy, its walkers per block) on the current device."""
+    n = ctypes.c_int64()
+    wpb = ctypes.c_int32()
+    _check(C.load().muca_optimal_walkers(L, layout, ctypes.byref(n), ctypes.byref(wpb)))
+    return n.value, wpb.value
 
 
 def muca_destroy(h) -> None:
@@ -238,6 +246,8 @@ class Muca:
         self.L, self.N, self.W = L, L * L, n_walkers
         self.n_bins = self.N + 1
         self._h = muca_create_ex(L, n_walkers, seed, layout, walkers_per_block)
+        if n_walkers == MUCA_WALKERS_OPTIMAL:
+            self.W = muca_get_info(self._h)[1]
         if stream is not None:
             handle = getattr(stream, "cuda_stream", stream)
             muca_set_stream(self._h, int(handle))

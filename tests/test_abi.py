@@ -47,7 +47,12 @@ def test_default_params_and_errors_without_gpu(lib):
     assert lib.muca_create(6, 10, 1, ctypes.byref(h)) == _lib.MUCA_EINVAL
     assert lib.muca_create(68, 10, 1, ctypes.byref(h)) == _lib.MUCA_EINVAL
     assert lib.muca_create(8, 0, 1, ctypes.byref(h)) == _lib.MUCA_EINVAL
+    assert lib.muca_create(8, -2, 1, ctypes.byref(h)) == _lib.MUCA_EINVAL
     assert lib.muca_sweep(None, 1, 0) == _lib.MUCA_EINVAL
+    n, wpb = ctypes.c_int64(), ctypes.c_int32()
+    assert lib.muca_optimal_walkers(6, 0, ctypes.byref(n), ctypes.byref(wpb)) == _lib.MUCA_EINVAL
+    assert lib.muca_optimal_walkers(32, _lib.MUCA_LAYOUT_AUTO, ctypes.byref(n), None) == _lib.MUCA_EINVAL
+    assert lib.muca_optimal_walkers(32, 0, None, None) == _lib.MUCA_EINVAL
 
 
 def test_missing_library_fails_loudly(monkeypatch, tmp_path):

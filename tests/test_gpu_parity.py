@@ -234,3 +234,33 @@ def test_invalid_arguments(muca_mod):
         bad[3] = np.nan
         with pytest.raises(muca_mod.MucaError):
             m.set_weights(bad)
+
+
+@pytest.mark.parametrize("L", [8, 32, 64])
+def test_optimal_walkers(muca_mod, orc, L):
+    """Default walker count (Sec. 3.1: full occupancy): a whole number of resident blocks
+    on every SM, and an instance created with it runs bit-exact (sampled walkers)."""
+    import torch
+    sms = torch.cuda.get_device_properties(0).multi_processor_count
+    n, wpb = muca_mod.muca_optimal_walkers(L)
+    assert wpb % 32 == 0 and 32 <= wpb <= 256
+    assert n > 0 and n % (sms * wpb) == 0
+    n_packed, _ = muca_mod.muca_optimal_walkers(L, muca_mod.MUCA_LAYOUT_PACKED)
+    assert n_packed > 0
+    if L != 32:
+        return
+    N = L * L
+    lnW = rand_weights(L, 11, 0.05)
+    with muca_mod.Muca(L, muca_mod.MUCA_WALKERS_OPTIMAL, 5) as m:
+        assert m.W == n
+        info = muca_mod.muca_get_info(m._h)
+        assert info[1] == n and info[4] == wpb
+        m.set_weights(lnW)
+        m.sweep(1, False)
+        e = m.get_energies()
+        lat = m.get_lattice()
+    T = orc.build_table(L, lnW)
+    for w in (0, n // 2 + 3, n - 1):
+        s, eo = orc.init(L, 5, 1, walker0=w)
+        orc.run(L, 5, s, eo, T, 0, N, False, None, walker0=w)
+        assert np.array_equal(lat[w], s[0]) and e[w] == eo[0] == e_index(L, lat[w])
