@@ -31,8 +31,8 @@
  *      t & 3; tag 0 = Metropolis, tag 1 = initial spins.  Initial spin at site i is +1
  *      iff the tag-1 word for t = i has its top bit clear.
  *   R3 integer acceptance: T = 0xFFFFFFFF if dw >= 0, else min(floor(exp(dw)*2^32),
- *      2^32-1) in FP64 with the C library exp; T = 0 if the target energy is off the
- *      grid.  A draw r is accepted iff r < T or T == 0xFFFFFFFF.
+ *      2^32-1) in FP64 with exp as in R8; T = 0 if the target energy is off the grid.
+ *      A draw r is accepted iff r < T or T == 0xFFFFFFFF.
  *   R4 recording: after every recorded attempt the post-decision energy is counted.
  *   R5 recursion: ln W(e) -= ln H(e) with raw counts, only where H(e) > 0.
  *   R6 accessible energies: every grid point except e = 1 and e = N - 1.
@@ -41,6 +41,12 @@
  *      histogram being tested (at least 10 of them), so that Q covers P's support and
  *      d_k >= 0 as Sec. 3 states; the schedule width w is the previous range's extent
  *      e_max - e_min + 1.
+ *   R8 the exp of the threshold table (R3), the ln of the recursion (R5) and the ln of
+ *      the Kullback-Leibler measure are orc_exp and orc_log below: a fixed sequence of
+ *      IEEE double operations (Cody-Waite reduction with a Taylor series; an atanh
+ *      series), so that a table built on another processor can be the same bit for bit.
+ *      The paper evaluates expf in FP32 (Sec. 2.3); the production estimate and the
+ *      reweighting keep the C library's exp and log.
  */
 #include <math.h>
 #include <stdint.h>
@@ -149,6 +155,94 @@ void orc_init(int32_t L, uint64_t seed, uint32_t walker0, int64_t nw, int8_t *sp
 }
 
 /* ---------------------------------------------------------------------------------
+ * exp and ln in FP64 (reading R8).  Every step is a single IEEE double operation
+ * (round to nearest, no fused multiply-add), so any machine evaluates them to the same
+ * bits; both stay within a few units in the last place of the C library's functions
+ * (checked by the tests).
+ * ------------------------------------------------------------------------------- */
+static const double ORC_LN2_HEAD = 0x1.62e42fee00000p-1;   /* ln 2 to 31 bits          */
+static const double ORC_LN2_TAIL = 0x1.a39ef35793c76p-33;  /* ln 2 - head, rounded     */
+static const double ORC_INV_LN2 = 0x1.71547652b82fep+0;    /* 1 / ln 2, rounded        */
+static const double ORC_SQRT2 = 0x1.6a09e667f3bcdp+0;      /* sqrt 2, rounded          */
+
+/* 2^k as a double for -1022 <= k <= 1023 (built from its exponent field). */
+static double orc_pow2i(int k)
+{
+    uint64_t b = (uint64_t)(k + 1023) << 52;
+    double d;
+    memcpy(&d, &b, sizeof d);
+    return d;
+}
+
+/* exp(x): Cody and Waite's reduction x = k ln 2 + r, k the integer nearest to x / ln 2
+ * and ln 2 split into a head whose multiples by k are exact and a tail; exp(r), |r| <=
+ * ln(2)/2, from its Taylor series through r^13 / 13! by Horner's rule (the remainder is
+ * below 5e-18); the result scaled by 2^k in two exact steps. */
+double orc_exp(double x)
+{
+    if (x != x)
+        return x;
+    if (x > 709.0)
+        return INFINITY;
+    if (x < -745.0)
+        return 0.0;
+    const double kd = floor(x * ORC_INV_LN2 + 0.5);
+    const double r = (x - kd * ORC_LN2_HEAD) - kd * ORC_LN2_TAIL;
+    /* 1/n! for n = 13 down to 0 */
+    const double inv_fact[14] = {1.0 / 6227020800.0, 1.0 / 479001600.0, 1.0 / 39916800.0, 1.0 / 3628800.0,
+                                 1.0 / 362880.0,     1.0 / 40320.0,     1.0 / 5040.0,     1.0 / 720.0,
+                                 1.0 / 120.0,        1.0 / 24.0,        1.0 / 6.0,        1.0 / 2.0,
+                                 1.0,                1.0};
+    double p = inv_fact[0];
+    for (int i = 1; i < 14; ++i)
+        p = p * r + inv_fact[i];
+    const int k = (int)kd;
+    const int k1 = k / 2, k2 = k - k1;
+    return (p * orc_pow2i(k1)) * orc_pow2i(k2);
+}
+
+/* ln(x), x > 0: x = 2^k m with m in [1/sqrt 2, sqrt 2], and
+ * ln m = 2 atanh(s) = 2 (s + s^3/3 + s^5/5 + ...), s = (m - 1)/(m + 1), |s| <= 0.172,
+ * summed through s^23 / 23 by Horner's rule in s^2 (the remainder is below 1e-18);
+ * ln x = k (ln 2 head) + (k (ln 2 tail) + ln m). */
+double orc_log(double x)
+{
+    if (x != x || x < 0.0)
+        return NAN;
+    if (x == 0.0)
+        return -INFINITY;
+    if (x == INFINITY)
+        return INFINITY;
+    int k = 0;
+    uint64_t b;
+    memcpy(&b, &x, sizeof b);
+    if (((b >> 52) & 0x7FFu) == 0u) {   /* subnormal: scale into the normal range */
+        x = x * orc_pow2i(54);
+        k = -54;
+        memcpy(&b, &x, sizeof b);
+    }
+    k += (int)((b >> 52) & 0x7FFu) - 1023;
+    b = (b & 0x000FFFFFFFFFFFFFull) | 0x3FF0000000000000ull;
+    double m;
+    memcpy(&m, &b, sizeof m);
+    if (m > ORC_SQRT2) {
+        m = m * 0.5;
+        k += 1;
+    }
+    const double s = (m - 1.0) / (m + 1.0);
+    const double z = s * s;
+    /* 1/(2n+1) for n = 11 down to 0 */
+    const double inv_odd[12] = {1.0 / 23.0, 1.0 / 21.0, 1.0 / 19.0, 1.0 / 17.0, 1.0 / 15.0, 1.0 / 13.0,
+                                1.0 / 11.0, 1.0 / 9.0,  1.0 / 7.0,  1.0 / 5.0,  1.0 / 3.0,  1.0};
+    double q = inv_odd[0];
+    for (int i = 1; i < 12; ++i)
+        q = q * z + inv_odd[i];
+    const double ln_m = (s + s) * q;
+    const double kd = (double)k;
+    return kd * ORC_LN2_HEAD + (kd * ORC_LN2_TAIL + ln_m);
+}
+
+/* ---------------------------------------------------------------------------------
  * Acceptance thresholds (Sec. 2.3, reading R3).  T[e*5 + k] is the threshold for a
  * flip at a site with k antiparallel neighbours from energy index e, which moves the
  * walker to e' = e + 2 - k (Delta E = 8 - 4k).
@@ -167,7 +261,7 @@ void orc_build_table(int32_t L, const double *lnW, uint32_t *T)
                 if (dw >= 0.0) {
                     thr = 0xFFFFFFFFu;
                 } else {
-                    double v = floor(exp(dw) * 4294967296.0);
+                    double v = floor(orc_exp(dw) * 4294967296.0);
                     thr = (v >= 4294967295.0) ? 0xFFFFFFFFu : (uint32_t)v;
                 }
             }
@@ -227,7 +321,7 @@ void orc_update_weights(int32_t L, double *lnW, const uint64_t *H)
     const int N = L * L;
     for (int e = 0; e <= N; ++e)
         if (H[e] > 0u)
-            lnW[e] -= log((double)H[e]);
+            lnW[e] -= orc_log((double)H[e]);
 }
 
 /* ---------------------------------------------------------------------------------
@@ -327,7 +421,7 @@ double orc_kullback_leibler(int32_t L, const uint64_t *H, double q)
         if (H[e] == 0u)
             continue;
         double P = (double)H[e] / total;
-        dk += P * log(P * q);
+        dk += P * orc_log(P * q);
     }
     return dk;
 }

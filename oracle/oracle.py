@@ -84,6 +84,8 @@ def lib():
                 "orc_accessible_in_range": (i32, [i32, P(u64)]),
                 "orc_kl_support": (i32, [i32, i32, i32, P(u64)]),
                 "orc_kullback_leibler": (dbl, [i32, P(u64), dbl]),
+                "orc_exp": (dbl, [dbl]),
+                "orc_log": (dbl, [dbl]),
                 "orc_chebyshev": (dbl, [i32, P(u64)]),
                 "orc_iterate": (i32, [i32, i64, u64, P(i8), P(i32), P(dbl), P(u64), P(Params),
                                       P(dbl), P(dbl), P(Result)]),
@@ -136,6 +138,16 @@ def init(L: int, seed: int, n_walkers: int, walker0: int = 0):
     e = np.zeros(n_walkers, dtype=np.int32)
     lib().orc_init(L, seed, walker0, n_walkers, _ptr(spins, ctypes.c_int8), _ptr(e, ctypes.c_int32))
     return spins, e
+
+
+def exp(x: float) -> float:
+    """The oracle's FP64 exp (reading R8)."""
+    return lib().orc_exp(float(x))
+
+
+def log(x: float) -> float:
+    """The oracle's FP64 natural logarithm (reading R8)."""
+    return lib().orc_log(float(x))
 
 
 def build_table(L: int, lnW: np.ndarray) -> np.ndarray:
