@@ -297,6 +297,15 @@ def run_native(args):
 
     lnW = m.get_weights()
     attempts_per_step = WALKERS * (THERM_SWEEPS + SWEEPS_PER_ITER) * N
+
+    # ---- the same, with the recursion, stop test and table build on the device ----
+    with M.Muca(L_SIDE, WALKERS, seed, layout=M.MUCA_LAYOUT_INT8, stream=stream) as md:
+        barrier(dist)
+        t0 = time.perf_counter()
+        st_dev = md.iterate_device(params, 8)
+        torch.cuda.synchronize()
+        ttf_dev = max_over_ranks(dist, time.perf_counter() - t0)
+        same_weights = bool(np.array_equal(md.get_weights(), lnW))
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
 
     def step(ev=None):
@@ -379,6 +388,8 @@ def run_native(args):
         "config": config_dict(),
         "time_to_flat_s": ttf,
         "iterations_to_flat": st.iterations,
+        "time_to_flat_device_iteration_s": ttf_dev,
+        "device_iteration_identical": bool(same_weights and st_dev.iterations == st.iterations),
         "flat": bool(st.converged),
         "flat_metric": st.last_metric,
         "therm_ms_per_step": sum(therm_ms) / len(therm_ms),
@@ -638,6 +649,158 @@ def run_fliptime_workload(args):
                    "layout": "int8 [site][walker]", "walkers_per_block": "occupancy rule"}}))
 
 
+def _oracle_production_shard(args):
+    """One host process of the CPU leg: its walkers thermalized, then n_chunks recorded
+    chunks of sweeps_per_chunk sweeps; returns the chunk histograms [n_chunks][N+1]."""
+    L, seed, w0, nw, lnW, therm, n_chunks, sweeps_per_chunk = args
+    import numpy as np
+    from oracle import oracle
+    N = L * L
+    s, e = oracle.init(L, seed, nw, walker0=w0)
+    T = oracle.build_table(L, np.asarray(lnW))
+    oracle.run(L, seed, s, e, T, 0, therm * N, False, None, walker0=w0)
+    t = therm * N
+    Hc = np.zeros((n_chunks, N + 1), dtype=np.uint64)
+    for c in range(n_chunks):
+        Hc[c] = oracle.run(L, seed, s, e, T, t, sweeps_per_chunk * N, True, None, walker0=w0)
+        t += sweeps_per_chunk * N
+    return Hc
+
+
+def run_production_workload(args):
+    """Production accuracy (Sec. 3.3, Fig. 7): walkers at full occupancy, weights
+    iterated to min/mean >= 0.8, thermalization for a fifth of the production sweeps,
+    then a production run of `--prod-seconds` split into 100 chunks; jackknife error
+    epsilon(E) and deviation Delta(E) = |ln g - ln g_exact| per energy.  CPU leg: the oracle on the host cores (one walker per process, the same
+    weights, the same wall time), and the statistical gain eps_cpu^2 / eps_gpu^2."""
+    import multiprocessing as mp
+    import numpy as np
+    import torch
+    import __graft_entry__
+    __graft_entry__.build()
+    from paper_1707_00919_gb300 import muca as M
+    dev = torch.cuda.current_device()
+    stream = torch.cuda.Stream()
+    chunks = 100
+    out = {}
+
+    def summary(g, err, exact):
+        acc = np.isfinite(exact)
+        d = np.abs(g[acc] - exact[acc])
+        ep = err[acc]
+        ok = np.isfinite(d) & np.isfinite(ep)   # bins seen in every leave-one-out estimate
+        mid = len(d) // 2
+        return {"max_delta": float(d[ok].max()), "mean_delta": float(d[ok].mean()), "delta_centre": float(d[mid]),
+                "median_eps": float(np.median(ep[ok])), "eps_centre": float(ep[mid]),
+                "max_eps": float(ep[ok].max()),
+                "frac_delta_within_2eps": float(np.mean(d[ok] <= 2 * ep[ok])), "bins_covered": int(ok.sum()),
+                "bins": int(acc.sum())}
+
+    with ClockSampler(dev) as clocks:
+        for L in (16, 32, 64):
+            N = L * L
+            exact = exact_ln_dos(L)
+            with M.Muca(L, M.MUCA_WALKERS_OPTIMAL, SEED, stream=stream) as m:
+                W = m.W
+                t0 = time.perf_counter()
+                st = m.iterate_until_flat(M.make_params(therm_sweeps=THERM_SWEEPS,
+                                                        sweeps_per_iter=10 if L <= 32 else 4, max_iterations=3000))
+                torch.cuda.synchronize()
+                flat_s = time.perf_counter() - t0
+                t_one = time_recorded_sweeps(m, stream, 4, 3) / 4
+                spc = max(1, int(args.prod_seconds / (t_one * chunks)))
+                therm = max(100, chunks * spc // 5)   # several round trips through the energy range
+                t0 = time.perf_counter()
+                _, g, err = m.production_jackknife(therm, chunks, spc)
+                prod_s = time.perf_counter() - t0
+                lnW = m.get_weights()
+            res = {"walkers": W, "iterations": st.iterations, "flat": bool(st.converged), "flat_s": flat_s,
+                   "production_s": prod_s, "sweeps_per_chunk": spc, "chunks": chunks, "therm_sweeps": therm,
+                   "attempts": W * spc * chunks * N, "gpu": summary(g, err, exact)}
+            if not args.no_cpu_baseline:
+                from oracle import oracle
+                oracle.build()
+                cores = os.cpu_count() or 1
+                rate_core = 4.0e7                    # calibrated below
+                s0, e0 = oracle.init(L, SEED, 1)
+                Tq = oracle.build_table(L, lnW)
+                tc = time.perf_counter()
+                oracle.run(L, SEED, s0, e0, Tq, 0, 20 * N, False)
+                rate_core = 20 * N / (time.perf_counter() - tc)
+                spc_cpu = max(1, int(args.prod_seconds * rate_core / (chunks * N)))
+                jobs = [(L, SEED, w, 1, list(lnW), max(100, chunks * spc_cpu // 5), chunks, spc_cpu)
+                        for w in range(cores)]
+                tc = time.perf_counter()
+                with mp.get_context("spawn").Pool(cores) as pool:
+                    parts = pool.map(_oracle_production_shard, jobs)
+                cpu_s = time.perf_counter() - tc
+                Hc = np.sum(np.stack(parts), axis=0).astype(np.uint64)
+                g_c, err_c = oracle.jackknife(L, lnW, Hc)
+                both = np.isfinite(exact) & (err > 0) & (err_c > 0) & np.isfinite(err) & np.isfinite(err_c)
+                res["cpu"] = summary(g_c, err_c, exact)
+                res["cpu"].update({"walkers": cores, "cores": cores, "sweeps_per_chunk": spc_cpu, "seconds": cpu_s})
+                res["statistical_gain_eps2"] = float(np.mean(err_c[both] ** 2 / err[both] ** 2)) if both.any() else None
+            out[f"L{L}"] = res
+    print(json.dumps({
+        "metric": "ln g accuracy from a fixed-time production run (jackknife eps vs exact Delta)",
+        "value": out["L32"]["gpu"]["max_delta"], "unit": "max |Delta ln g|", "higher_is_better": False,
+        "n_gpus": 1, "production": out, "clocks": clocks.summary(),
+        "data": "synthetic: random +/-1 start, weights iterated from ln W = 0",
+        "config": {"workload": "production_L16_L32_L64", "seconds_per_L": args.prod_seconds,
+                   "walkers": "full occupancy (Sec. 3.1 rule)", "chunks": chunks,
+                   "stop_rule": "min/mean >= 0.8"}}))
+
+
+def run_convergence_workload(args):
+    """Iterations and time until the weights converge against the walker count (the
+    protocol of Figs. 3 and 4, Sec. 3.2): Eq. (7) schedule, stop when d_k < 1e-4
+    (Eq. (6)), from ln W = 0, `--seeds` independent seeds per point; mean, standard error
+    and median of each."""
+    import numpy as np
+    import torch
+    import __graft_entry__
+    __graft_entry__.build()
+    from paper_1707_00919_gb300 import muca as M
+    dev = torch.cuda.current_device()
+    stream = torch.cuda.Stream()
+    cases = {16: [1024, 2048, 4096, 8192, 16384, 32768], 32: [4096, 8192, 16384, 32768, 65536]}
+    params = M.make_params(schedule=M.MUCA_SCHEDULE_PAPER, stop_rule=M.MUCA_STOP_KL, flat_threshold=1e-4,
+                           max_iterations=3000)
+    out = {}
+    with ClockSampler(dev) as clocks:
+        for L, Ws in cases.items():
+            rows = []
+            for W in Ws:
+                its, secs, atts, conv = [], [], [], 0
+                for seed in range(1, args.seeds + 1):
+                    with M.Muca(L, W, seed, stream=stream) as m:
+                        torch.cuda.synchronize()
+                        t0 = time.perf_counter()
+                        st = m.iterate_until_flat(params)
+                        torch.cuda.synchronize()
+                        secs.append(time.perf_counter() - t0)
+                    its.append(st.iterations)
+                    atts.append(st.attempts_per_walker * W)
+                    conv += int(st.converged)
+
+                def stats(v):
+                    v = np.asarray(v, dtype=np.float64)
+                    return {"mean": float(v.mean()), "err": float(v.std(ddof=1) / math.sqrt(len(v))) if len(v) > 1
+                            else 0.0, "median": float(np.median(v))}
+                rows.append({"walkers": W, "iterations": stats(its), "seconds": stats(secs),
+                             "attempts": stats(atts), "converged": conv, "runs": args.seeds})
+            out[f"L{L}"] = rows
+    l32 = {r["walkers"]: r for r in out["L32"]}
+    print(json.dumps({
+        "metric": "time until converged weights vs walkers (Eq. (7) schedule, d_k < 1e-4)",
+        "value": l32[16384]["seconds"]["mean"], "unit": "s", "higher_is_better": False, "n_gpus": 1,
+        "convergence": out, "clocks": clocks.summary(),
+        "data": "synthetic: random +/-1 start per seed, ln W = 0",
+        "config": {"workload": "convergence_vs_walkers_L16_L32", "seeds": args.seeds,
+                   "schedule": "Eq. (7): N_therm = 30 w, N_upd = floor(6 w^2.25 / W) + 1, x1.1 after full range",
+                   "stop_rule": "Kullback-Leibler d_k < 1e-4", "max_iterations": 3000}}))
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -645,7 +808,10 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["native", "reference"], default="native")
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--workload", choices=["headline", "batch", "serve", "fliptime"], default="headline")
+    ap.add_argument("--workload", choices=["headline", "batch", "serve", "fliptime", "convergence", "production"],
+                    default="headline")
+    ap.add_argument("--seeds", type=int, default=32)
+    ap.add_argument("--prod-seconds", type=float, default=10.0)
     ap.add_argument("--serve-seconds", type=float, default=2.0)
     args = ap.parse_args()
     if args.workload == "batch":
@@ -656,6 +822,12 @@ def main():
         return
     if args.workload == "fliptime":
         run_fliptime_workload(args)
+        return
+    if args.workload == "convergence":
+        run_convergence_workload(args)
+        return
+    if args.workload == "production":
+        run_production_workload(args)
         return
     if args.warmup < 3 and args.impl == "native":
         args.warmup = 3

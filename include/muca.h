@@ -25,8 +25,12 @@
  *   - Acceptance (Sec. 2.3, integer form): for a flip at a site with k antiparallel
  *     neighbours the energy index moves to e' = e + 2 - k; with dw = lnW[e'] - lnW[e]
  *     the threshold is 0xFFFFFFFF if dw >= 0, else min(floor(exp(dw) * 2^32), 2^32 - 1)
- *     computed on the host in FP64, and 0 if e' is off the grid.  A draw r is
- *     accepted iff r < T or T == 0xFFFFFFFF.
+ *     in FP64, and 0 if e' is off the grid.  A draw r is accepted iff r < T or
+ *     T == 0xFFFFFFFF.
+ *   - exp (thresholds) and ln (the Eq. (4) recursion, the Eq. (6) measure) are a fixed
+ *     sequence of IEEE double operations: Cody-Waite reduction with the Taylor series of
+ *     exp, and the atanh series of ln (within 1 and 3 units in the last place of the C
+ *     library's exp and log), so the host and the device compute the same bits.
  *   - Recording: each recorded attempt adds its post-decision energy index to H.
  *
  * Memory and threads
@@ -191,6 +195,28 @@ int muca_reset_histogram(muca_t h);
  * Returns MUCA_OK, MUCA_ENOTCONVERGED or MUCA_ETIMEOUT (stats filled in every case),
  * or another error.  p == NULL uses muca_default_params; stats may be NULL. */
 int muca_iterate_until_flat(muca_t h, const muca_params *p, muca_stats *stats);
+
+/* The same weight iteration with its host-side steps on the device: after each recorded
+ * phase kernels test the stop rule, apply Eq. (4) and build the next threshold table,
+ * so no histogram or table crosses to the host between iterations.  The host enqueues
+ * iterations_per_sync (>= 1) iterations at a time and then reads a small state record;
+ * iterations enqueued after the stop do nothing.  Fixed-sweep schedule only
+ * (MUCA_SCHEDULE_SWEEPS; the Eq. (7) schedule sizes each iteration from the previous
+ * histogram on the host).  Weights, table, histogram, lattices, energies, attempt
+ * counter and stats equal those of muca_iterate_until_flat bit for bit, except that a
+ * deadline is checked only every iterations_per_sync iterations.  Returns as
+ * muca_iterate_until_flat; MUCA_EINVAL also for another schedule or
+ * iterations_per_sync < 1.  Allocates (N + 1) doubles and a state record on the device
+ * at the first call. */
+int muca_iterate_device(muca_t h, const muca_params *p, int32_t iterations_per_sync, muca_stats *stats);
+
+/* Host computations of the library without an instance (no device needed).
+ * muca_build_table: thresholds T_out[e*5 + k] (n_bins = L*L + 1 weights in, 5 n_bins
+ * thresholds out) by the rule above.  muca_update_weights: Eq. (4) in logarithms,
+ * lnW[e] -= ln H[e] where H[e] > 0, in place.  Errors: MUCA_EINVAL (L as in muca_create,
+ * wrong n_bins, NULL, non-finite weight). */
+int muca_build_table(int32_t L, const double *lnW, size_t n_bins, uint32_t *T_out);
+int muca_update_weights(int32_t L, double *lnW, const uint64_t *H, size_t n_bins);
 
 /* Production run (Sec. 3.3) with the current weights: therm_sweeps unrecorded sweeps,
  * zero H, n_sweeps recorded sweeps, then ln g(e) = ln H(e) - ln W(e) on visited energies

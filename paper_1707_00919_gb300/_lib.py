@@ -89,6 +89,9 @@ SIGNATURES = {
     "muca_create": (ctypes.c_int, [ctypes.c_int32, ctypes.c_int64, ctypes.c_uint64, _P(_H)]),
     "muca_create_ex": (ctypes.c_int, [_P(muca_options), _P(_H)]),
     "muca_optimal_walkers": (ctypes.c_int, [ctypes.c_int32, ctypes.c_int32, _P(ctypes.c_int64), _P(ctypes.c_int32)]),
+    "muca_iterate_device": (ctypes.c_int, [_H, _P(muca_params), ctypes.c_int32, _P(muca_stats)]),
+    "muca_build_table": (ctypes.c_int, [ctypes.c_int32, _P(ctypes.c_double), ctypes.c_size_t, _P(ctypes.c_uint32)]),
+    "muca_update_weights": (ctypes.c_int, [ctypes.c_int32, _P(ctypes.c_double), _P(ctypes.c_uint64), ctypes.c_size_t]),
     "muca_destroy": (ctypes.c_int, [_H]),
     "muca_set_stream": (ctypes.c_int, [_H, ctypes.c_void_p]),
     "muca_set_allocator": (ctypes.c_int, [ALLOC_FN, RELEASE_FN, ctypes.c_void_p]),

@@ -19,6 +19,7 @@
 
 #include "../../include/muca.h"
 #include "muca_internal.h"
+#include "muca_math.cuh"
 
 namespace {
 
@@ -109,6 +110,10 @@ struct muca_s {
     uint32_t *h_err = nullptr;
     cudaEvent_t table_copied = nullptr;    // last table upload has left h_table
     std::vector<double> lnW;
+    void *iter_block = nullptr;      // device ln W and iteration state (muca_iterate_device)
+    double *d_lnW = nullptr;
+    muca::IterState *d_iter = nullptr;
+    muca::IterState *h_iter = nullptr;   // pinned staging of the state
     uint64_t t = 0;                  // attempt counter (tag 0 stream)
     int32_t kl_lo = -1, kl_hi = -1;  // range visited in the previous batched iteration
 };
@@ -124,13 +129,7 @@ void build_table(int32_t L, const std::vector<double> &lnW, uint32_t *T)
             const int32_t to = e + 2 - k;
             uint32_t v = 0u;
             if (to >= 0 && to <= N) {
-                const double dw = lnW[(size_t)to] - lnW[(size_t)e];
-                if (dw >= 0.0) {
-                    v = 0xFFFFFFFFu;
-                } else {
-                    const double scaled = std::floor(std::exp(dw) * 4294967296.0);
-                    v = scaled >= 4294967295.0 ? 0xFFFFFFFFu : (uint32_t)scaled;
-                }
+                v = muca::fp64::threshold(lnW[(size_t)to] - lnW[(size_t)e]);
             }
             T[(size_t)e * 5 + (size_t)k] = v;
         }
@@ -165,7 +164,7 @@ int sync_and_check(muca_t h)
     return check_device_error(h);
 }
 
-int run_attempts(muca_t h, uint64_t n, bool record)
+int run_attempts(muca_t h, uint64_t n, bool record, const uint32_t *skip = nullptr)
 {
     const uint64_t cap = record ? max_recorded_attempts(h->wpb) : UINT64_MAX;
     while (n > 0) {
@@ -182,6 +181,7 @@ int run_attempts(muca_t h, uint64_t n, bool record)
         a.table = h->d_table;
         a.hist = h->d_hist;
         a.err = h->d_err;
+        a.skip = skip;
         MUCA_CUDA(muca::launch_sweep(a, h->wpb, record, h->stream), "sweep launch");
         h->t += chunk;
         n -= chunk;
@@ -232,7 +232,7 @@ double kullback_leibler(int32_t N, const std::vector<uint64_t> &H, double q)
     for (int32_t e = 0; e <= N; ++e)
         if (H[(size_t)e]) {
             const double p = (double)H[(size_t)e] / sum;
-            d += p * std::log(p * q);
+            d += p * muca::fp64::log(p * q);
         }
     return d;
 }
@@ -603,7 +603,7 @@ bool member_update(muca_t h, const muca_params &p, muca_stats &s)
     }
     for (int32_t e = 0; e <= N; ++e)
         if (H[(size_t)e])
-            h->lnW[(size_t)e] -= std::log((double)H[(size_t)e]);
+            h->lnW[(size_t)e] -= muca::fp64::log((double)H[(size_t)e]);
     if (!visited_range(N, H, h->kl_lo, h->kl_hi))
         h->kl_lo = h->kl_hi = -1;
     return s.iterations >= p.max_iterations;
@@ -833,6 +833,9 @@ int muca_destroy(muca_t h)
     if (h->stream)
         cudaStreamSynchronize(h->stream);
     device_free(h->alloc, h->block);
+    device_free(h->alloc, h->iter_block);
+    if (h->h_iter)
+        cudaFreeHost(h->h_iter);
     if (h->h_table)
         cudaFreeHost(h->h_table);
     if (h->h_hist)
@@ -1010,7 +1013,7 @@ int muca_iterate_until_flat(muca_t h, const muca_params *p_in, muca_stats *stats
         // Eq. (4) in logarithms: ln W <- ln W - ln H on visited energies.
         for (int32_t e = 0; e <= N; ++e)
             if (H[(size_t)e])
-                h->lnW[(size_t)e] -= std::log((double)H[(size_t)e]);
+                h->lnW[(size_t)e] -= muca::fp64::log((double)H[(size_t)e]);
         int32_t lo, hi;
         if (visited_range(N, H, lo, hi)) {
             prev_width = hi - lo + 1;
@@ -1045,6 +1048,128 @@ int muca_iterate_until_flat(muca_t h, const muca_params *p_in, muca_stats *stats
     if (timed_out)
         return fail(MUCA_ETIMEOUT, "deadline of %.3f s passed after %d iterations", p.deadline_s, n);
     return fail(MUCA_ENOTCONVERGED, "histogram not flat after %d iterations (metric %g)", n, metric);
+}
+
+int muca_build_table(int32_t L, const double *lnW, size_t n_bins, uint32_t *T_out)
+{
+    if (L < 4 || L > 64 || L % 4 != 0)
+        return fail(MUCA_EINVAL, "L = %d: must be a multiple of 4 in [4, 64]", L);
+    if (!lnW || !T_out || n_bins != (size_t)L * L + 1)
+        return fail(MUCA_EINVAL, "need %d weights and a table buffer", L * L + 1);
+    for (size_t e = 0; e < n_bins; ++e)
+        if (!std::isfinite(lnW[e]))
+            return fail(MUCA_EINVAL, "ln W[%zu] is not finite", e);
+    build_table(L, std::vector<double>(lnW, lnW + n_bins), T_out);
+    return MUCA_OK;
+}
+
+int muca_update_weights(int32_t L, double *lnW, const uint64_t *H, size_t n_bins)
+{
+    if (L < 4 || L > 64 || L % 4 != 0)
+        return fail(MUCA_EINVAL, "L = %d: must be a multiple of 4 in [4, 64]", L);
+    if (!lnW || !H || n_bins != (size_t)L * L + 1)
+        return fail(MUCA_EINVAL, "need %d weights and histogram counts", L * L + 1);
+    for (size_t e = 0; e < n_bins; ++e)
+        if (H[e])
+            lnW[e] -= muca::fp64::log((double)H[e]);
+    return MUCA_OK;
+}
+
+int muca_iterate_device(muca_t h, const muca_params *p_in, int32_t iterations_per_sync, muca_stats *stats)
+{
+    int rc = validate(h);
+    if (rc)
+        return rc;
+    muca_params p;
+    if (p_in)
+        p = *p_in;
+    else
+        muca_default_params(&p);
+    if (p.schedule != MUCA_SCHEDULE_SWEEPS)
+        return fail(MUCA_EINVAL, "muca_iterate_device runs the fixed-sweep schedule only");
+    if (p.stop_rule < MUCA_STOP_MIN_MEAN || p.stop_rule > MUCA_STOP_CHEBYSHEV)
+        return fail(MUCA_EINVAL, "unknown stop rule %d", p.stop_rule);
+    if (p.max_iterations < 1)
+        return fail(MUCA_EINVAL, "max_iterations must be positive");
+    if (iterations_per_sync < 1)
+        return fail(MUCA_EINVAL, "iterations_per_sync must be positive");
+    const auto start = std::chrono::steady_clock::now();
+    const int32_t N = h->N;
+    const size_t nb = (size_t)N + 1;
+    if (!h->iter_block) {
+        const size_t off_state = align256(nb * sizeof(double));
+        h->iter_block = device_alloc(h->alloc, off_state + align256(sizeof(muca::IterState)));
+        if (!h->iter_block)
+            return fail(MUCA_ENOMEM, "device allocation for the iteration state failed");
+        h->d_lnW = static_cast<double *>(h->iter_block);
+        h->d_iter = reinterpret_cast<muca::IterState *>(static_cast<char *>(h->iter_block) + off_state);
+        MUCA_CUDA(cudaMallocHost(reinterpret_cast<void **>(&h->h_iter), sizeof(muca::IterState)),
+                  "pinned iteration state");
+        MUCA_CUDA(muca::configure_iter_metric(N), "metric kernel shared memory");
+    }
+    const uint64_t n_therm = p.therm_sweeps * (uint64_t)N, n_upd = p.sweeps_per_iter * (uint64_t)N;
+    const uint64_t t_start = h->t;
+    // the first table and the weights from the host; the state zeroed
+    MUCA_CUDA(cudaStreamSynchronize(h->stream), "stream synchronize");
+    std::memset(h->h_iter, 0, sizeof(muca::IterState));
+    h->h_iter->prev_lo = -1;
+    h->h_iter->prev_hi = -1;
+    MUCA_CUDA(cudaMemcpyAsync(h->d_iter, h->h_iter, sizeof(muca::IterState), cudaMemcpyHostToDevice, h->stream),
+              "iteration state upload");
+    MUCA_CUDA(cudaMemcpyAsync(h->d_lnW, h->lnW.data(), nb * sizeof(double), cudaMemcpyHostToDevice, h->stream),
+              "weights upload");
+    rc = upload_table(h);
+    if (rc)
+        return rc;
+    const uint32_t *done = &h->d_iter->done;
+    int32_t enqueued = 0;
+    bool timed_out = false;
+    for (;;) {
+        const int32_t batch = std::min(iterations_per_sync, p.max_iterations - enqueued);
+        for (int32_t i = 0; i < batch; ++i) {
+            if ((rc = run_attempts(h, n_therm, false, done)) != MUCA_OK)
+                return rc;
+            MUCA_CUDA(muca::launch_iter_reset_hist(h->d_hist, (int32_t)nb, h->d_iter, h->stream), "histogram reset");
+            if ((rc = run_attempts(h, n_upd, true, done)) != MUCA_OK)
+                return rc;
+            MUCA_CUDA(muca::launch_iter_metric(h->d_iter, N, h->d_hist, p.stop_rule, p.flat_threshold,
+                                               p.max_iterations, h->stream),
+                      "metric launch");
+            MUCA_CUDA(muca::launch_iter_recursion(h->d_iter, N, h->d_lnW, h->d_hist, h->stream), "recursion launch");
+            MUCA_CUDA(muca::launch_iter_table(h->d_iter, N, h->d_lnW, h->d_table, h->stream), "table launch");
+        }
+        enqueued += batch;
+        MUCA_CUDA(cudaMemcpyAsync(h->h_iter, h->d_iter, sizeof(muca::IterState), cudaMemcpyDeviceToHost, h->stream),
+                  "iteration state read");
+        if ((rc = sync_and_check(h)) != MUCA_OK)
+            return rc;
+        if (h->h_iter->done || enqueued >= p.max_iterations)
+            break;
+        if (p.deadline_s > 0.0 &&
+            std::chrono::duration<double>(std::chrono::steady_clock::now() - start).count() > p.deadline_s) {
+            timed_out = true;
+            break;
+        }
+    }
+    const muca::IterState st = *h->h_iter;
+    // launches after the last tested iteration did nothing: the counter covers the rest
+    h->t = t_start + (uint64_t)st.iterations * (n_therm + n_upd);
+    MUCA_CUDA(cudaMemcpyAsync(h->lnW.data(), h->d_lnW, nb * sizeof(double), cudaMemcpyDeviceToHost, h->stream),
+              "weights read");
+    MUCA_CUDA(cudaStreamSynchronize(h->stream), "stream synchronize");
+    const bool flat = st.done == 1u;
+    if (stats) {
+        stats->iterations = st.iterations;
+        stats->converged = flat ? 1 : 0;
+        stats->last_metric = st.metric;
+        stats->attempts_per_walker = (uint64_t)st.iterations * (n_therm + n_upd);
+        stats->seconds = std::chrono::duration<double>(std::chrono::steady_clock::now() - start).count();
+    }
+    if (flat)
+        return MUCA_OK;
+    if (timed_out)
+        return fail(MUCA_ETIMEOUT, "deadline of %.3f s passed after %d iterations", p.deadline_s, st.iterations);
+    return fail(MUCA_ENOTCONVERGED, "histogram not flat after %d iterations (metric %g)", st.iterations, st.metric);
 }
 
 int muca_production(muca_t h, uint64_t therm_sweeps, uint64_t n_sweeps, uint64_t *H_out, double *ln_g_out,

@@ -420,6 +420,8 @@ template <int L, bool RECORD, bool PARTIAL = false>
 __device__ __forceinline__ void sweep_block(const SweepArgs &a, int64_t wbase, int wpb, unsigned char *smem,
                                             const int LAYOUT)
 {
+    if (a.skip && *a.skip)   // an iteration run on the device has finished
+        return;
     using RowT = typename RowOf<L>::type;
     constexpr int N = L * L;
     constexpr int NB = N + 1;

@@ -30,7 +30,31 @@ struct SweepArgs {
     const uint32_t *table;      // [(N+1)*5]
     unsigned long long *hist;   // [N+1], accumulated when recording
     uint32_t *err;              // device error word
+    const uint32_t *skip = nullptr;   // when set and nonzero at launch: the launch does nothing
 };
+
+// Device state of an iteration whose recursion runs on the device (muca_iterate_device).
+struct IterState {
+    uint32_t done;       // 0: running; 1: the last histogram was flat; 2: iteration limit
+    uint32_t update;     // the last metric asked for the recursion and the next table
+    int32_t iterations;  // iterations whose histogram was tested
+    int32_t prev_lo;     // energy range visited in the previous iteration (-1: none)
+    int32_t prev_hi;
+    int32_t pad;
+    double metric;       // stop metric of the last tested histogram
+};
+
+// The steps of one device-side iteration after its recorded sweeps (muca_iterate.cu):
+// zeroing the histogram (skipped once done), the stop metric (one block; skipped once
+// done), the Eq. (4) recursion and the table of the next iteration (both only when the
+// metric kernel set `update`).
+cudaError_t launch_iter_reset_hist(unsigned long long *hist, int32_t nb, const IterState *st, cudaStream_t s);
+cudaError_t configure_iter_metric(int32_t N);
+cudaError_t launch_iter_metric(IterState *st, int32_t N, const unsigned long long *hist, int32_t stop_rule,
+                               double flat_threshold, int32_t max_iterations, cudaStream_t s);
+cudaError_t launch_iter_recursion(const IterState *st, int32_t N, double *lnW, const unsigned long long *hist,
+                                  cudaStream_t s);
+cudaError_t launch_iter_table(const IterState *st, int32_t N, const double *lnW, uint32_t *table, cudaStream_t s);
 
 // One work item of the batched kernel: walkers wbase .. wbase + wpb - 1 of instance inst.
 struct BatchItem {

@@ -47,6 +47,8 @@ template <typename RowT, int LAYOUT, bool RECORD>
 __global__ void __launch_bounds__(1024) sweep_kernel(const SweepArgs a)
 {
     extern __shared__ __align__(16) unsigned char smem[];
+    if (a.skip && *a.skip)   // an iteration run on the device has finished
+        return;
     const int L = a.L;
     const int N = L * L;
     const int nb = N + 1;

@@ -151,6 +151,30 @@ def muca_iterate_until_flat(h, params: muca_params | None = None, raise_on_fail:
     return rc, st
 
 
+def muca_iterate_device(h, params: muca_params | None = None, iterations_per_sync: int = 8,
+                        raise_on_fail: bool = True):
+    st = muca_stats()
+    rc = C.load().muca_iterate_device(h, ctypes.byref(params) if params is not None else None,
+                                       iterations_per_sync, ctypes.byref(st))
+    if raise_on_fail:
+        _check(rc)
+    return rc, st
+
+
+def muca_build_table(L: int, lnW) -> np.ndarray:
+    w = np.ascontiguousarray(lnW, dtype=np.float64)
+    T = np.zeros(5 * w.size, dtype=np.uint32)
+    _check(C.load().muca_build_table(L, _p(w, ctypes.c_double), w.size, _p(T, ctypes.c_uint32)))
+    return T
+
+
+def muca_update_weights(L: int, lnW: np.ndarray, H) -> None:
+    """Eq. (4) in place on a float64 array."""
+    assert lnW.dtype == np.float64 and lnW.flags["C_CONTIGUOUS"]
+    h = np.ascontiguousarray(H, dtype=np.uint64)
+    _check(C.load().muca_update_weights(L, _p(lnW, ctypes.c_double), _p(h, ctypes.c_uint64), lnW.size))
+
+
 def muca_production(h, therm_sweeps: int, n_sweeps: int, n_bins: int):
     H = np.zeros(n_bins, dtype=np.uint64)
     g = np.zeros(n_bins, dtype=np.float64)
@@ -294,6 +318,12 @@ class Muca:
 
     def iterate_until_flat(self, params: muca_params | None = None, raise_on_fail: bool = False) -> IterationStats:
         rc, st = muca_iterate_until_flat(self._h, params, raise_on_fail)
+        return IterationStats(rc, st.iterations, bool(st.converged), st.last_metric, st.attempts_per_walker,
+                              st.seconds)
+
+    def iterate_device(self, params: muca_params | None = None, iterations_per_sync: int = 8,
+                       raise_on_fail: bool = False) -> IterationStats:
+        rc, st = muca_iterate_device(self._h, params, iterations_per_sync, raise_on_fail)
         return IterationStats(rc, st.iterations, bool(st.converged), st.last_metric, st.attempts_per_walker,
                               st.seconds)
 

@@ -1,0 +1,66 @@
+"""The library's host-side arithmetic against the oracle, without a GPU: threshold tables
+(Sec. 2.3 rule, FP64 exp of reading R8) and the Eq. (4) recursion (FP64 ln), bit for
+bit, on weights that reach every branch of the rule (always accept, exp underflowing the
+2^-32 grid, exp rounding to 1, off-grid targets)."""
+import math
+
+import numpy as np
+import pytest
+
+
+@pytest.fixture(scope="module")
+def mm():
+    from paper_1707_00919_gb300 import build
+    build.build()
+    from paper_1707_00919_gb300 import muca
+    return muca
+
+
+@pytest.mark.parametrize("L", [4, 8, 16, 32, 64])
+@pytest.mark.parametrize("scale", [1e-9, 0.3, 3.0, 30.0])
+def test_table_matches_oracle(mm, orc, L, scale):
+    rng = np.random.default_rng(L * 1000 + int(scale * 10))
+    lnW = np.cumsum(rng.normal(0.0, scale, L * L + 1))
+    T = mm.muca_build_table(L, lnW)
+    To = orc.build_table(L, lnW)
+    assert np.array_equal(T, To)
+
+
+def test_table_branches(mm, orc):
+    L = 4
+    N = L * L
+    lnW = np.zeros(N + 1)
+    lnW[6] = -math.log(2.0)
+    lnW[9] = -60.0
+    lnW[12] = -1e-18
+    T = mm.muca_build_table(L, lnW).reshape(N + 1, 5)
+    assert np.array_equal(T.ravel(), orc.build_table(L, lnW))
+    assert T[5, 1] == 2 ** 31 and T[8, 1] == 0 and T[11, 1] == 0xFFFFFFFF and T[0, 4] == 0
+
+
+@pytest.mark.parametrize("L", [4, 32, 64])
+def test_recursion_matches_oracle(mm, orc, L):
+    rng = np.random.default_rng(L)
+    N = L * L
+    lnW = rng.normal(0.0, 5.0, N + 1)
+    H = rng.integers(0, 2 ** 40, N + 1).astype(np.uint64)
+    H[rng.random(N + 1) < 0.3] = 0
+    H[:3] = [1, 2, 2 ** 53]
+    a, b = lnW.copy(), lnW.copy()
+    mm.muca_update_weights(L, a, H)
+    orc.update_weights(L, b, H)
+    assert np.array_equal(a, b)
+    assert np.array_equal(a[H == 0], lnW[H == 0])
+
+
+def test_host_helpers_reject_bad_arguments(mm):
+    with pytest.raises(mm.MucaError):
+        mm.muca_build_table(6, np.zeros(37))
+    with pytest.raises(mm.MucaError):
+        mm.muca_build_table(4, np.zeros(16))
+    bad = np.zeros(17)
+    bad[2] = np.inf
+    with pytest.raises(mm.MucaError):
+        mm.muca_build_table(4, bad)
+    with pytest.raises(mm.MucaError):
+        mm.muca_update_weights(4, np.zeros(16), np.zeros(16, dtype=np.uint64))
