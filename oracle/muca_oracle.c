@@ -41,6 +41,10 @@
  *      histogram being tested (at least 10 of them), so that Q covers P's support and
  *      d_k >= 0 as Sec. 3 states; the schedule width w is the previous range's extent
  *      e_max - e_min + 1.
+ *   R9 random site order (the paper's scheme of Sec. 2.3, an alternative to R1): the
+ *      site of attempt t, the same for every walker, is floor(u N / 2^32) with u the
+ *      Philox word t & 3 of counter (t >> 2, walker word 0xFFFFFFFF, tag 2); the
+ *      acceptance word of walker w is the one of R2.
  *   R8 the exp of the threshold table (R3), the ln of the recursion (R5) and the ln of
  *      the Kullback-Leibler measure are orc_exp and orc_log below: a fixed sequence of
  *      IEEE double operations (Cody-Waite reduction with a Taylor series; an atanh
@@ -55,6 +59,8 @@
 
 #define ORC_TAG_METROPOLIS 0u
 #define ORC_TAG_INIT 1u
+#define ORC_TAG_SITE 2u
+#define ORC_SHARED_STREAM 0xFFFFFFFFu   /* walker word of the site stream (R9) */
 
 /* ---------------------------------------------------------------------------------
  * Philox4x32-10 (Salmon, Moraes, Dror, Shaw, SC'11): ten rounds of two 32x32->64 bit
@@ -313,6 +319,49 @@ void orc_run(int32_t L, uint64_t seed, uint32_t walker0, int64_t nw, int8_t *spi
     }
 }
 
+/* Site of attempt t in random order (R9): one shared stream for all walkers. */
+int32_t orc_random_site(int32_t L, uint64_t seed, uint64_t t)
+{
+    const uint32_t u = orc_random_word(seed, ORC_SHARED_STREAM, ORC_TAG_SITE, t);
+    return (int32_t)(((uint64_t)u * (uint64_t)(L * L)) >> 32);
+}
+
+/* The same updates with the sites of R9 instead of typewriter order (Sec. 2.3: one
+ * random site sequence for all walkers, an independent acceptance stream per walker). */
+void orc_run_random(int32_t L, uint64_t seed, uint32_t walker0, int64_t nw, int8_t *spins, int32_t *e,
+                    const uint32_t *T, uint64_t t0, uint64_t n, int32_t record, uint64_t *H)
+{
+    const int N = L * L;
+    for (int64_t w = 0; w < nw; ++w) {
+        const uint32_t walker = walker0 + (uint32_t)w;
+        int8_t *s = spins + w * (int64_t)N;
+        int32_t ew = e[w];
+        for (uint64_t t = t0; t < t0 + n; ++t) {
+            const uint32_t r = orc_random_word(seed, walker, ORC_TAG_METROPOLIS, t);
+            const int i = orc_random_site(L, seed, t);
+            const int x = i % L, y = i / L;
+            const int k = orc_antiparallel(L, s, x, y);
+            if (orc_accept(r, T[ew * 5 + k])) {
+                s[i] = (int8_t)(-s[i]);
+                ew += 2 - k;
+            }
+            if (record)
+                H[ew] += 1u;
+        }
+        e[w] = ew;
+    }
+}
+
+/* Updates in the order the parameters ask for. */
+static void orc_update(int32_t order, int32_t L, uint64_t seed, int64_t nw, int8_t *spins, int32_t *e,
+                       const uint32_t *T, uint64_t t0, uint64_t n, int32_t record, uint64_t *H)
+{
+    if (order == 1)
+        orc_run_random(L, seed, 0u, nw, spins, e, T, t0, n, record, H);
+    else
+        orc_run(L, seed, 0u, nw, spins, e, T, t0, n, record, H);
+}
+
 /* ---------------------------------------------------------------------------------
  * Weight recursion, Eq. (4), in logarithms (reading R5).
  * ------------------------------------------------------------------------------- */
@@ -463,6 +512,7 @@ typedef struct {
     double factor;
     double growth;           /* schedule 1: after full coverage, floor(growth N) + 1 */
     int32_t max_iterations;
+    int32_t site_order;      /* 0: typewriter (R1); 1: random shared sites (R9)      */
 } orc_params;
 
 typedef struct {
@@ -535,10 +585,10 @@ int32_t orc_iterate(int32_t L, int64_t nw, uint64_t seed, int8_t *spins, int32_t
         if (lnW_history)
             memcpy(lnW_history + (size_t)n * (N + 1), lnW, sizeof(double) * (N + 1));
         orc_build_table(L, lnW, T);
-        orc_run(L, seed, 0u, nw, spins, e, T, t, n_therm, 0, NULL);
+        orc_update(p->site_order, L, seed, nw, spins, e, T, t, n_therm, 0, NULL);
         t += n_therm;
         memset(H, 0, sizeof(uint64_t) * (N + 1));
-        orc_run(L, seed, 0u, nw, spins, e, T, t, n_upd, 1, H);
+        orc_update(p->site_order, L, seed, nw, spins, e, T, t, n_upd, 1, H);
         t += n_upd;
         spent += n_therm + n_upd;
         const double q = (double)orc_kl_support(L, prev_lo, prev_hi, H);
@@ -603,7 +653,7 @@ void orc_ln_dos(int32_t L, const double *lnW, const uint64_t *H, double *ln_g)
 
 int32_t orc_production(int32_t L, int64_t nw, uint64_t seed, int8_t *spins, int32_t *e,
                        const double *lnW, uint64_t *t_inout, uint64_t therm_sweeps,
-                       uint64_t sweeps, uint64_t *H, double *ln_g)
+                       uint64_t sweeps, uint64_t *H, double *ln_g, int32_t site_order)
 {
     const int N = L * L;
     uint32_t *T = (uint32_t *)malloc(((size_t)N + 1) * 5 * sizeof(uint32_t));
@@ -611,10 +661,10 @@ int32_t orc_production(int32_t L, int64_t nw, uint64_t seed, int8_t *spins, int3
         return -1;
     uint64_t t = *t_inout;
     orc_build_table(L, lnW, T);
-    orc_run(L, seed, 0u, nw, spins, e, T, t, therm_sweeps * (uint64_t)N, 0, NULL);
+    orc_update(site_order, L, seed, nw, spins, e, T, t, therm_sweeps * (uint64_t)N, 0, NULL);
     t += therm_sweeps * (uint64_t)N;
     memset(H, 0, sizeof(uint64_t) * (N + 1));
-    orc_run(L, seed, 0u, nw, spins, e, T, t, sweeps * (uint64_t)N, 1, H);
+    orc_update(site_order, L, seed, nw, spins, e, T, t, sweeps * (uint64_t)N, 1, H);
     t += sweeps * (uint64_t)N;
     orc_ln_dos(L, lnW, H, ln_g);
     *t_inout = t;

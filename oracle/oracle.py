@@ -47,6 +47,7 @@ class Params(ctypes.Structure):
         ("factor", ctypes.c_double),
         ("growth", ctypes.c_double),
         ("max_iterations", ctypes.c_int32),
+        ("site_order", ctypes.c_int32),
     ]
 
 
@@ -77,6 +78,8 @@ def lib():
                 "orc_build_table": (None, [i32, P(dbl), P(u32)]),
                 "orc_accept": (ctypes.c_int, [u32, u32]),
                 "orc_run": (None, [i32, u64, u32, i64, P(i8), P(i32), P(u32), u64, u64, i32, P(u64)]),
+                "orc_run_random": (None, [i32, u64, u32, i64, P(i8), P(i32), P(u32), u64, u64, i32, P(u64)]),
+                "orc_random_site": (i32, [i32, u64, u64]),
                 "orc_update_weights": (None, [i32, P(dbl), P(u64)]),
                 "orc_accessible": (ctypes.c_int, [i32, i32]),
                 "orc_min_over_mean": (dbl, [i32, P(u64)]),
@@ -91,7 +94,7 @@ def lib():
                                       P(dbl), P(dbl), P(Result)]),
                 "orc_ln_dos": (None, [i32, P(dbl), P(u64), P(dbl)]),
                 "orc_production": (i32, [i32, i64, u64, P(i8), P(i32), P(dbl), P(u64), u64, u64,
-                                         P(u64), P(dbl)]),
+                                         P(u64), P(dbl), i32]),
                 "orc_dos_bruteforce": (i32, [i32, P(u64)]),
                 "orc_jackknife": (i32, [i32, P(dbl), P(u64), i32, P(dbl), P(dbl)]),
                 "orc_canonical": (None, [i32, P(dbl), dbl, P(dbl), P(dbl)]),
@@ -150,6 +153,11 @@ def log(x: float) -> float:
     return lib().orc_log(float(x))
 
 
+def random_site(L: int, seed: int, t: int) -> int:
+    """Site of attempt t in random shared order (reading R9)."""
+    return lib().orc_random_site(L, seed, t)
+
+
 def build_table(L: int, lnW: np.ndarray) -> np.ndarray:
     lnW = np.ascontiguousarray(lnW, dtype=np.float64)
     assert lnW.shape == (L * L + 1,)
@@ -159,17 +167,18 @@ def build_table(L: int, lnW: np.ndarray) -> np.ndarray:
 
 
 def run(L: int, seed: int, spins: np.ndarray, e: np.ndarray, T: np.ndarray, t0: int, n: int,
-        record: bool, H: np.ndarray | None = None, walker0: int = 0) -> np.ndarray | None:
-    """Advances the walkers in place by n attempts from attempt counter t0."""
+        record: bool, H: np.ndarray | None = None, walker0: int = 0, site_order: int = 0) -> np.ndarray | None:
+    """Advances the walkers in place by n attempts from attempt counter t0 (site_order 0:
+    typewriter, reading R1; 1: random shared sites, reading R9)."""
     assert spins.dtype == np.int8 and spins.flags["C_CONTIGUOUS"]
     assert e.dtype == np.int32 and e.flags["C_CONTIGUOUS"]
     nw = spins.shape[0]
     if record and H is None:
         H = np.zeros(L * L + 1, dtype=np.uint64)
     Hp = _ptr(H, ctypes.c_uint64) if H is not None else None
-    lib().orc_run(L, seed, walker0, nw, _ptr(spins, ctypes.c_int8), _ptr(e, ctypes.c_int32),
-                  _ptr(np.ascontiguousarray(T, dtype=np.uint32), ctypes.c_uint32), t0, n,
-                  1 if record else 0, Hp)
+    fn = lib().orc_run_random if site_order == 1 else lib().orc_run
+    fn(L, seed, walker0, nw, _ptr(spins, ctypes.c_int8), _ptr(e, ctypes.c_int32),
+       _ptr(np.ascontiguousarray(T, dtype=np.uint32), ctypes.c_uint32), t0, n, 1 if record else 0, Hp)
     return H
 
 
@@ -198,9 +207,9 @@ def accessible_in_range(L: int, H: np.ndarray) -> int:
 
 
 def make_params(schedule=0, stop_rule=0, flat_threshold=0.8, therm_sweeps=31, sweeps_per_iter=100,
-                f_therm=30.0, z=2.25, factor=6.0, growth=1.1, max_iterations=200) -> Params:
+                f_therm=30.0, z=2.25, factor=6.0, growth=1.1, max_iterations=200, site_order=0) -> Params:
     return Params(schedule, stop_rule, flat_threshold, therm_sweeps, sweeps_per_iter, f_therm, z,
-                  factor, growth, max_iterations)
+                  factor, growth, max_iterations, site_order)
 
 
 def iterate(L: int, seed: int, spins: np.ndarray, e: np.ndarray, lnW: np.ndarray, t: int,
@@ -237,7 +246,7 @@ def ln_dos(L: int, lnW: np.ndarray, H: np.ndarray) -> np.ndarray:
 
 
 def production(L: int, seed: int, spins: np.ndarray, e: np.ndarray, lnW: np.ndarray, t: int,
-               therm_sweeps: int, sweeps: int):
+               therm_sweeps: int, sweeps: int, site_order: int = 0):
     """Returns (H, ln_g, t)."""
     N = L * L
     H = np.zeros(N + 1, dtype=np.uint64)
@@ -247,7 +256,7 @@ def production(L: int, seed: int, spins: np.ndarray, e: np.ndarray, lnW: np.ndar
                               _ptr(e, ctypes.c_int32),
                               _ptr(np.ascontiguousarray(lnW, dtype=np.float64), ctypes.c_double),
                               ctypes.byref(tt), therm_sweeps, sweeps, _ptr(H, ctypes.c_uint64),
-                              _ptr(ln_g, ctypes.c_double))
+                              _ptr(ln_g, ctypes.c_double), site_order)
     if rc != 0:
         raise MemoryError("orc_production failed")
     return H, ln_g, int(tt.value)
