@@ -329,6 +329,9 @@ def run_native(args):
             ev[3].record(stream)
         return H
 
+    # NVTX range around the warm-up and timed steps, so that a profiler can be limited to
+    # them (ncu --nvtx --nvtx-include "bench_steps/")
+    torch.cuda.nvtx.range_push("bench_steps")
     for _ in range(args.warmup):
         step()
         with torch.cuda.stream(stream):
@@ -345,6 +348,7 @@ def run_native(args):
                 flush.zero_()
         stream.synchronize()
         torch.cuda.synchronize()
+    torch.cuda.nvtx.range_pop()
     step_ms = [evs[k][0].elapsed_time(evs[k][3]) for k in range(args.steps)]
     therm_ms = [evs[k][0].elapsed_time(evs[k][1]) for k in range(args.steps)]
     rec_ms = [evs[k][1].elapsed_time(evs[k][2]) for k in range(args.steps)]
@@ -413,9 +417,20 @@ def run_native(args):
     pp_s = time_recorded_sweeps(mp_, stream, SWEEPS_PER_ITER, 7)
     mp_.close()
     pp_rate = WALKERS * SWEEPS_PER_ITER * N / pp_s
+    # the paper's random shared site order (Sec. 2.3) on the same workload
+    mr = M.Muca(L_SIDE, WALKERS, seed, layout=M.MUCA_LAYOUT_INT8, stream=stream)
+    mr.site_order = M.MUCA_ORDER_RANDOM
+    mr.set_weights(perfect_weights(L_SIDE))
+    mr.sweep(3, record=False)
+    rnd_s = time_recorded_sweeps(mr, stream, 2, 5)
+    mr.close()
+    rnd_rate = WALKERS * 2 * N / rnd_s
     result["paper_protocol"] = {"attempts_per_s": pp_rate, "ns_per_flip": 1e9 / pp_rate,
                                 "protocol": f"ln W = -ln g exact, {THERM_SWEEPS} sweeps to equilibrate, "
                                             f"median of 7 launches of {SWEEPS_PER_ITER} recorded sweeps"}
+    result["random_site_order"] = {"attempts_per_s": rnd_rate, "ns_per_flip": 1e9 / rnd_rate,
+                                   "protocol": "perfect weights, 3 sweeps to equilibrate, median of 5 launches "
+                                               "of 2 recorded sweeps in random shared site order"}
     if rank == 0 and not args.no_cpu_baseline:
         rate, cores, wall = cpu_baseline(lnW, WALKERS)
         result["cpu_baseline"] = {"value": rate, "unit": "attempts/s", "cores": cores, "kind": "oracle",

@@ -155,6 +155,19 @@ int muca_optimal_walkers(int32_t L, int32_t layout, int64_t *n_walkers, int32_t 
 /* Frees all device and host memory of the instance (NULL is accepted). */
 int muca_destroy(muca_t h);
 
+/* Site order of later updates (sweeps, attempts, iterations, production):
+ * MUCA_ORDER_TYPEWRITER (default): attempt t flips site t mod N;
+ * MUCA_ORDER_RANDOM: the paper's scheme (Sec. 2.3), one random site sequence shared by
+ * all walkers, the site of attempt t being floor(u N / 2^32) with u the Philox word t & 3
+ * of counter (t >> 2, 0xFFFFFFFF, tag 2); acceptance words as in typewriter order.
+ * Random order runs on its own kernel (any L and attempt range); the batched entry
+ * points run typewriter order only and reject instances in random order.
+ * Errors: MUCA_EINVAL (NULL, unknown order). */
+#define MUCA_ORDER_TYPEWRITER 0
+#define MUCA_ORDER_RANDOM 1
+int muca_set_site_order(muca_t h, int32_t order);
+int muca_get_site_order(muca_t h, int32_t *order);
+
 /* Runs the instance's work on the given cudaStream_t (passed as void*; NULL = the
  * instance's own stream).  Work already queued on the old stream is synchronized first. */
 int muca_set_stream(muca_t h, void *cuda_stream);

@@ -25,6 +25,8 @@ MUCA_LAYOUT_PACKED = 1
 MUCA_LAYOUT_AUTO = 2
 MUCA_WPB_TUNE = -1
 MUCA_WALKERS_OPTIMAL = -1
+MUCA_ORDER_TYPEWRITER = 0
+MUCA_ORDER_RANDOM = 1
 
 MUCA_STOP_MIN_MEAN = 0
 MUCA_STOP_KL = 1
@@ -90,6 +92,8 @@ SIGNATURES = {
     "muca_create_ex": (ctypes.c_int, [_P(muca_options), _P(_H)]),
     "muca_optimal_walkers": (ctypes.c_int, [ctypes.c_int32, ctypes.c_int32, _P(ctypes.c_int64), _P(ctypes.c_int32)]),
     "muca_iterate_device": (ctypes.c_int, [_H, _P(muca_params), ctypes.c_int32, _P(muca_stats)]),
+    "muca_set_site_order": (ctypes.c_int, [_H, ctypes.c_int32]),
+    "muca_get_site_order": (ctypes.c_int, [_H, _P(ctypes.c_int32)]),
     "muca_build_table": (ctypes.c_int, [ctypes.c_int32, _P(ctypes.c_double), ctypes.c_size_t, _P(ctypes.c_uint32)]),
     "muca_update_weights": (ctypes.c_int, [ctypes.c_int32, _P(ctypes.c_double), _P(ctypes.c_uint64), ctypes.c_size_t]),
     "muca_destroy": (ctypes.c_int, [_H]),

@@ -115,6 +115,7 @@ struct muca_s {
     muca::IterState *d_iter = nullptr;
     muca::IterState *h_iter = nullptr;   // pinned staging of the state
     uint64_t t = 0;                  // attempt counter (tag 0 stream)
+    int32_t order = MUCA_ORDER_TYPEWRITER;   // site order of the updates
     int32_t kl_lo = -1, kl_hi = -1;  // range visited in the previous batched iteration
 };
 
@@ -182,7 +183,10 @@ int run_attempts(muca_t h, uint64_t n, bool record, const uint32_t *skip = nullp
         a.hist = h->d_hist;
         a.err = h->d_err;
         a.skip = skip;
-        MUCA_CUDA(muca::launch_sweep(a, h->wpb, record, h->stream), "sweep launch");
+        if (h->order == MUCA_ORDER_RANDOM)
+            MUCA_CUDA(muca::launch_random_sweep(a, record, h->stream), "random-order sweep launch");
+        else
+            MUCA_CUDA(muca::launch_sweep(a, h->wpb, record, h->stream), "sweep launch");
         h->t += chunk;
         n -= chunk;
     }
@@ -850,6 +854,28 @@ int muca_destroy(muca_t h)
     return MUCA_OK;
 }
 
+int muca_set_site_order(muca_t h, int32_t order)
+{
+    int rc = validate(h);
+    if (rc)
+        return rc;
+    if (order != MUCA_ORDER_TYPEWRITER && order != MUCA_ORDER_RANDOM)
+        return fail(MUCA_EINVAL, "unknown site order %d", order);
+    h->order = order;
+    return MUCA_OK;
+}
+
+int muca_get_site_order(muca_t h, int32_t *order)
+{
+    int rc = validate(h);
+    if (rc)
+        return rc;
+    if (!order)
+        return fail(MUCA_EINVAL, "NULL argument");
+    *order = h->order;
+    return MUCA_OK;
+}
+
 int muca_set_stream(muca_t h, void *cuda_stream)
 {
     int rc = validate(h);
@@ -1296,6 +1322,8 @@ int muca_batch_create(const muca_t *instances, int32_t n, muca_batch_t *out)
         if (!batchable_L(instances[i]->L))
             return fail(MUCA_EINVAL, "instance %d: L = %d has no whole-sweep kernel (8, 16, 24, 32, 48, 64)", i,
                         instances[i]->L);
+        if (instances[i]->order != MUCA_ORDER_TYPEWRITER)
+            return fail(MUCA_EINVAL, "instance %d: the batched kernel runs typewriter order only", i);
         for (int32_t j = 0; j < i; ++j)
             if (instances[j] == instances[i])
                 return fail(MUCA_EINVAL, "instance %d appears twice", i);

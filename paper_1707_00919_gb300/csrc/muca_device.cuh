@@ -58,6 +58,31 @@ struct RowOf {
 };
 
 
+// Philox4x32-10 of Salmon et al. (SC'11), the generator of Sec. 2.3, on counter c with
+// key (k0, k1).
+__device__ __forceinline__ uint4 philox4x32_10(uint4 c, uint32_t k0, uint32_t k1)
+{
+#pragma unroll
+    for (int round = 0; round < 10; ++round) {
+        if (round > 0) {
+            k0 += 0x9E3779B9u;
+            k1 += 0xBB67AE85u;
+        }
+        const uint32_t lo0 = 0xD2511F53u * c.x;
+        const uint32_t hi0 = __umulhi(0xD2511F53u, c.x);
+        const uint32_t lo1 = 0xCD9E8D57u * c.z;
+        const uint32_t hi1 = __umulhi(0xCD9E8D57u, c.z);
+        c = make_uint4(hi1 ^ c.y ^ k0, lo1, hi0 ^ c.w ^ k1, lo0);
+    }
+    return c;
+}
+
+// Counter tags of the Philox streams: updates, initial spins, random site order.
+constexpr uint32_t kTagMetropolis = 0u;
+constexpr uint32_t kTagInit = 1u;
+constexpr uint32_t kTagSite = 2u;
+constexpr uint32_t kSharedStream = 0xFFFFFFFFu;   // walker word of the site stream
+
 struct PhiloxKeys {
     uint32_t k0[10], k1[10];   // round keys
     uint32_t hi_w, lo_w;       // round-0 product of the walker counter word

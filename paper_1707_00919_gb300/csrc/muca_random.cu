@@ -1,0 +1,195 @@
+// muca_random.cu - updates in random shared site order, the paper's scheme of Sec. 2.3:
+// one random site sequence drives all walkers (so a warp's accesses to a site coincide)
+// and each walker draws its acceptance from its own stream.  The site of attempt t is
+// floor(u N / 2^32) with u the Philox word t & 3 of counter (t >> 2, 0xFFFFFFFF, tag 2);
+// the acceptance word is the one of typewriter order (tag 0, the walker's counter).
+//
+// One thread runs one walker; its lattice sits in shared memory as one bit row per
+// lattice row ([row][walker-in-block]); the block draws the sites of a chunk of
+// attempts into shared memory together, then every walker runs the chunk.
+#include <algorithm>
+#include <cstdint>
+
+#include "muca_device.cuh"
+
+namespace muca {
+namespace {
+
+constexpr int kSiteChunk = 1024;   // attempts whose sites are drawn at once
+
+template <typename RowT>
+size_t random_smem_bytes_t(int L, int wpb, bool record)
+{
+    const size_t nb = (size_t)L * L + 1;
+    return align_up((nb * 5 + (record ? nb : 0)) * 4 + (size_t)kSiteChunk * 2, 16) + (size_t)L * wpb * sizeof(RowT);
+}
+
+template <typename RowT, int LAYOUT, bool RECORD>
+__global__ void __launch_bounds__(256) random_sweep_kernel(const SweepArgs a)
+{
+    extern __shared__ __align__(16) unsigned char smem[];
+    if (a.skip && *a.skip)   // an iteration run on the device has finished
+        return;
+    const int L = a.L;
+    const int N = L * L;
+    const int nb = N + 1;
+    const int wpb = blockDim.x;
+    uint32_t *sT = reinterpret_cast<uint32_t *>(smem);
+    uint32_t *sH = sT + nb * 5;
+    uint16_t *sSite = reinterpret_cast<uint16_t *>(sH + (RECORD ? nb : 0));
+    RowT *sRows = reinterpret_cast<RowT *>(smem + align_up((size_t)(nb * 5 + (RECORD ? nb : 0)) * 4 +
+                                                               (size_t)kSiteChunk * 2, 16));
+    const int tid = threadIdx.x;
+    const int64_t w = (int64_t)blockIdx.x * wpb + tid;
+    bool active = w < a.W;
+
+    for (int i = tid; i < nb * 5; i += wpb)
+        sT[i] = a.table[i];
+    if (RECORD)
+        for (int i = tid; i < nb; i += wpb)
+            sH[i] = 0u;
+    RowT *col = sRows + tid;   // this walker's rows: col[y * wpb]
+    int32_t e = 0;
+    if (active) {
+        if (LAYOUT == MUCA_LAYOUT_PACKED) {
+            const RowT *g = reinterpret_cast<const RowT *>(a.lattice);
+            for (int y = 0; y < L; ++y)
+                col[y * wpb] = g[(size_t)y * a.W + w];
+        } else {
+            const int8_t *g = reinterpret_cast<const int8_t *>(a.lattice);
+            for (int y = 0; y < L; ++y) {
+                RowT r = 0;
+                for (int x = 0; x < L; ++x)
+                    r |= (RowT)(g[(size_t)(y * L + x) * a.W + w] < 0) << x;
+                col[y * wpb] = r;
+            }
+        }
+        e = a.energy[w];
+        if (e < 0 || e > N) {
+            atomicOr(a.err, kErrEnergyRange);
+            active = false;
+        }
+    }
+    const uint32_t k0 = (uint32_t)a.seed, k1 = (uint32_t)(a.seed >> 32);
+    const uint32_t wid = (uint32_t)w;
+    const uint64_t tend = a.t0 + a.n;
+    uint64_t cached = ~0ull;
+    uint4 words = make_uint4(0u, 0u, 0u, 0u);
+    for (uint64_t tc = a.t0; tc < tend; tc += kSiteChunk) {
+        const int m = tend - tc < (uint64_t)kSiteChunk ? (int)(tend - tc) : kSiteChunk;
+        __syncthreads();   // the previous chunk's sites are consumed (and the setup done)
+        for (int j = tid; j < m; j += wpb) {
+            const uint64_t t = tc + (uint64_t)j;
+            const uint64_t blk = t >> 2;
+            const uint4 q = philox4x32_10(make_uint4((uint32_t)blk, (uint32_t)(blk >> 32), kSharedStream, kTagSite),
+                                          k0, k1);
+            const uint32_t u = (t & 3) == 0 ? q.x : (t & 3) == 1 ? q.y : (t & 3) == 2 ? q.z : q.w;
+            const uint32_t i = __umulhi(u, (uint32_t)N);
+            const uint32_t y = i / (uint32_t)L;
+            sSite[j] = (uint16_t)((y << 8) | (i - y * (uint32_t)L));
+        }
+        __syncthreads();
+        if (!active)
+            continue;
+        for (int j = 0; j < m; ++j) {
+            const uint64_t t = tc + (uint64_t)j;
+            if ((t >> 2) != cached) {
+                cached = t >> 2;
+                words = philox4x32_10(make_uint4((uint32_t)cached, (uint32_t)(cached >> 32), wid, kTagMetropolis),
+                                      k0, k1);
+            }
+            const uint32_t r = (t & 3) == 0 ? words.x : (t & 3) == 1 ? words.y : (t & 3) == 2 ? words.z : words.w;
+            const uint32_t p = sSite[j];
+            const int y = (int)(p >> 8), x = (int)(p & 0xFFu);
+            const int yu = (y == 0) ? L - 1 : y - 1;
+            const int yd = (y == L - 1) ? 0 : y + 1;
+            const int xl = (x == 0) ? L - 1 : x - 1;
+            const int xr = (x == L - 1) ? 0 : x + 1;
+            const RowT C = col[y * wpb];
+            const uint32_t sx = bit_at(C, x);
+            const uint32_t k = (sx ^ bit_at(col[yu * wpb], x)) + (sx ^ bit_at(col[yd * wpb], x)) +
+                               (sx ^ bit_at(C, xl)) + (sx ^ bit_at(C, xr));
+            const uint32_t thr = sT[e * 5 + (int)k];
+            if (r < thr || thr == 0xFFFFFFFFu) {
+                col[y * wpb] = C ^ ((RowT)1 << x);
+                e += 2 - (int)k;
+            }
+            if (RECORD)
+                atomicAdd(&sH[e], 1u);
+        }
+    }
+    __syncthreads();
+    if (RECORD)
+        for (int i = tid; i < nb; i += wpb) {
+            const uint32_t v = sH[i];
+            if (v)
+                atomicAdd(&a.hist[i], (unsigned long long)v);
+        }
+    if (active) {
+        if (LAYOUT == MUCA_LAYOUT_PACKED) {
+            RowT *g = reinterpret_cast<RowT *>(a.lattice);
+            for (int y = 0; y < L; ++y)
+                g[(size_t)y * a.W + w] = col[y * wpb];
+        } else {
+            int8_t *g = reinterpret_cast<int8_t *>(a.lattice);
+            for (int y = 0; y < L; ++y) {
+                const RowT r = col[y * wpb];
+                for (int x = 0; x < L; ++x)
+                    g[(size_t)(y * L + x) * a.W + w] = bit_at(r, x) ? (int8_t)-1 : (int8_t)1;
+            }
+        }
+        a.energy[w] = e;
+    }
+}
+
+template <typename RowT, int LAYOUT, bool RECORD>
+cudaError_t launch_random_t(const SweepArgs &a, int wpb, cudaStream_t s)
+{
+    const size_t smem = random_smem_bytes_t<RowT>(a.L, wpb, RECORD);
+    auto kern = random_sweep_kernel<RowT, LAYOUT, RECORD>;
+    if (smem > 48 * 1024) {
+        const cudaError_t err = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (err != cudaSuccess)
+            return err;
+    }
+    const int64_t blocks = (a.W + wpb - 1) / wpb;
+    kern<<<(unsigned)blocks, wpb, smem, s>>>(a);
+    return cudaGetLastError();
+}
+
+template <typename RowT>
+cudaError_t launch_random_row(const SweepArgs &a, int wpb, bool record, cudaStream_t s)
+{
+    if (a.layout == MUCA_LAYOUT_PACKED)
+        return record ? launch_random_t<RowT, MUCA_LAYOUT_PACKED, true>(a, wpb, s)
+                      : launch_random_t<RowT, MUCA_LAYOUT_PACKED, false>(a, wpb, s);
+    return record ? launch_random_t<RowT, MUCA_LAYOUT_INT8, true>(a, wpb, s)
+                  : launch_random_t<RowT, MUCA_LAYOUT_INT8, false>(a, wpb, s);
+}
+
+}  // namespace
+
+size_t random_smem_bytes(int L, int wpb, bool record)
+{
+    return L <= 32 ? random_smem_bytes_t<uint32_t>(L, wpb, record)
+                   : random_smem_bytes_t<unsigned long long>(L, wpb, record);
+}
+
+cudaError_t launch_random_sweep(const SweepArgs &a, bool record, cudaStream_t s)
+{
+    if (a.n == 0 || a.W == 0)
+        return cudaSuccess;
+    // the largest block of whole warps whose rows fit next to the table, histogram and
+    // site buffer (the walker-to-thread mapping does not affect the result)
+    const size_t limit = sweep_smem_limit();
+    int wpb = 256;
+    while (wpb > 32 && random_smem_bytes(a.L, wpb, record) > limit)
+        wpb -= 32;
+    if (random_smem_bytes(a.L, wpb, record) > limit)
+        return cudaErrorInvalidConfiguration;
+    if (a.L <= 32)
+        return launch_random_row<uint32_t>(a, wpb, record, s);
+    return launch_random_row<unsigned long long>(a, wpb, record, s);
+}
+
+}  // namespace muca

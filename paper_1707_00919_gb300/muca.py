@@ -14,7 +14,8 @@ import numpy as np
 
 from . import _lib as C
 from ._lib import (MUCA_LAYOUT_AUTO, MUCA_LAYOUT_INT8, MUCA_LAYOUT_PACKED, MUCA_OK,  # noqa: F401
-                   MUCA_SCHEDULE_PAPER, MUCA_WALKERS_OPTIMAL, MUCA_WPB_TUNE,
+                   MUCA_ORDER_RANDOM, MUCA_ORDER_TYPEWRITER, MUCA_SCHEDULE_PAPER, MUCA_WALKERS_OPTIMAL,
+                   MUCA_WPB_TUNE,
                    MUCA_SCHEDULE_SWEEPS, MUCA_STOP_CHEBYSHEV, MUCA_STOP_KL, MUCA_STOP_MIN_MEAN,
                    muca_options, muca_params, muca_stats)
 
@@ -89,6 +90,16 @@ def muca_create_ex(L: int, n_walkers: int, seed: int, layout: int = MUCA_LAYOUT_
     h = ctypes.c_void_p()
     _check(C.load().muca_create_ex(ctypes.byref(o), ctypes.byref(h)))
     return h
+
+
+def muca_set_site_order(h, order: int) -> None:
+    _check(C.load().muca_set_site_order(h, order))
+
+
+def muca_get_site_order(h) -> int:
+    o = ctypes.c_int32()
+    _check(C.load().muca_get_site_order(h, ctypes.byref(o)))
+    return o.value
 
 
 def muca_optimal_walkers(L: int, layout: int = MUCA_LAYOUT_INT8) -> tuple[int, int]:
@@ -320,6 +331,14 @@ class Muca:
         rc, st = muca_iterate_until_flat(self._h, params, raise_on_fail)
         return IterationStats(rc, st.iterations, bool(st.converged), st.last_metric, st.attempts_per_walker,
                               st.seconds)
+
+    @property
+    def site_order(self) -> int:
+        return muca_get_site_order(self._h)
+
+    @site_order.setter
+    def site_order(self, order: int) -> None:
+        muca_set_site_order(self._h, order)
 
     def iterate_device(self, params: muca_params | None = None, iterations_per_sync: int = 8,
                        raise_on_fail: bool = False) -> IterationStats:
