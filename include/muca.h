@@ -64,6 +64,7 @@ extern "C" {
 #define MUCA_ETIMEOUT (-4)       /* the deadline of muca_iterate_until_flat passed          */
 #define MUCA_ENOTCONVERGED (-5)  /* the iteration budget ran out before H was flat          */
 #define MUCA_EDEVICE (-6)        /* a kernel reported an invalid state                      */
+#define MUCA_EIO (-7)            /* a checkpoint file could not be written or read, or is not one */
 
 /* Lattice storage layouts in device memory (both walker-minor, Sec. 2.3: all walkers'
  * copies of one site are adjacent, so a warp's accesses coalesce). */
@@ -154,6 +155,27 @@ int muca_optimal_walkers(int32_t L, int32_t layout, int64_t *n_walkers, int32_t 
 
 /* Frees all device and host memory of the instance (NULL is accepted). */
 int muca_destroy(muca_t h);
+
+/* State and checkpoints.  The state of an instance is its lattices, energies, ln W, the
+ * histogram, the attempt counter and the site order (the random numbers are a function of
+ * seed, walker and attempt counter, Sec. 2.3), so a restored instance continues bit for
+ * bit as the saved one would have.
+ * muca_set_lattice: replaces the lattices by spins[walker][site] (int8 +1 / -1,
+ * n = n_walkers * N) and recomputes the energies on the device.
+ * muca_set_attempt_counter: sets t, the counter of the next attempt.
+ * muca_save: writes the state and the creation options to a binary file (little-endian:
+ * 8-byte magic "MUCACKP1", L, layout, n_walkers, seed, walkers_per_block, site order, t,
+ * ln W[N+1] FP64, H[N+1] uint64, energies int32[n_walkers], then per walker N bits,
+ * rounded up to whole bytes, bit i of byte i/8 set for a down spin at site i).
+ * muca_load: creates an instance from such a file (same options) and restores the state;
+ * the stored energies must equal those recomputed from the stored lattices.
+ * Errors: MUCA_EINVAL (NULL, wrong n, a spin other than +1 / -1), MUCA_EIO (file
+ * cannot be opened, written or read; not a checkpoint; inconsistent content),
+ * MUCA_ENOMEM, MUCA_ECUDA. */
+int muca_set_lattice(muca_t h, const int8_t *spins, size_t n);
+int muca_set_attempt_counter(muca_t h, uint64_t t);
+int muca_save(muca_t h, const char *path);
+int muca_load(const char *path, muca_t *out);
 
 /* Site order of later updates (sweeps, attempts, iterations, production):
  * MUCA_ORDER_TYPEWRITER (default): attempt t flips site t mod N;

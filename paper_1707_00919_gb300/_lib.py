@@ -19,6 +19,7 @@ MUCA_ECUDA = -3
 MUCA_ETIMEOUT = -4
 MUCA_ENOTCONVERGED = -5
 MUCA_EDEVICE = -6
+MUCA_EIO = -7
 
 MUCA_LAYOUT_INT8 = 0
 MUCA_LAYOUT_PACKED = 1
@@ -93,6 +94,10 @@ SIGNATURES = {
     "muca_optimal_walkers": (ctypes.c_int, [ctypes.c_int32, ctypes.c_int32, _P(ctypes.c_int64), _P(ctypes.c_int32)]),
     "muca_iterate_device": (ctypes.c_int, [_H, _P(muca_params), ctypes.c_int32, _P(muca_stats)]),
     "muca_set_site_order": (ctypes.c_int, [_H, ctypes.c_int32]),
+    "muca_set_lattice": (ctypes.c_int, [_H, _P(ctypes.c_int8), ctypes.c_size_t]),
+    "muca_set_attempt_counter": (ctypes.c_int, [_H, ctypes.c_uint64]),
+    "muca_save": (ctypes.c_int, [_H, ctypes.c_char_p]),
+    "muca_load": (ctypes.c_int, [ctypes.c_char_p, _P(_H)]),
     "muca_get_site_order": (ctypes.c_int, [_H, _P(ctypes.c_int32)]),
     "muca_build_table": (ctypes.c_int, [ctypes.c_int32, _P(ctypes.c_double), ctypes.c_size_t, _P(ctypes.c_uint32)]),
     "muca_update_weights": (ctypes.c_int, [ctypes.c_int32, _P(ctypes.c_double), _P(ctypes.c_uint64), ctypes.c_size_t]),

@@ -121,6 +121,31 @@ struct muca_s {
 
 namespace {
 
+// Checkpoint files (muca_save / muca_load).
+const char kCheckpointMagic[8] = {'M', 'U', 'C', 'A', 'C', 'K', 'P', '1'};
+
+struct FileCloser {
+    FILE *f;
+    ~FileCloser()
+    {
+        if (f)
+            std::fclose(f);
+    }
+};
+
+template <typename T>
+bool put(FILE *f, const T *v, size_t n)
+{
+    return std::fwrite(v, sizeof(T), n, f) == n;
+}
+
+template <typename T>
+bool get(FILE *f, T *v, size_t n)
+{
+    return std::fread(v, sizeof(T), n, f) == n;
+}
+
+
 // Acceptance thresholds from ln W (Sec. 2.3, integer form): see muca.h.
 void build_table(int32_t L, const std::vector<double> &lnW, uint32_t *T)
 {
@@ -1262,6 +1287,138 @@ int muca_get_lattice(muca_t h, int8_t *out, size_t n)
     if (err != cudaSuccess)
         return cuda_fail(err, "lattice read");
     return sync_and_check(h);
+}
+
+int muca_set_lattice(muca_t h, const int8_t *spins, size_t n)
+{
+    int rc = validate(h);
+    if (rc)
+        return rc;
+    const size_t total = (size_t)h->W * (size_t)h->N;
+    if (!spins || n != total)
+        return fail(MUCA_EINVAL, "lattice has %zu entries", total);
+    for (size_t i = 0; i < total; ++i)
+        if (spins[i] != 1 && spins[i] != -1)
+            return fail(MUCA_EINVAL, "spin %zu is %d, not +1 or -1", i, (int)spins[i]);
+    int8_t *tmp = static_cast<int8_t *>(device_alloc(h->alloc, total));
+    if (!tmp)
+        return fail(MUCA_ENOMEM, "device allocation of %zu bytes failed", total);
+    cudaError_t err = cudaMemcpyAsync(tmp, spins, total, cudaMemcpyHostToDevice, h->stream);
+    if (err == cudaSuccess)
+        err = muca::launch_pack(h->L, h->layout, h->W, tmp, h->d_lattice, h->d_energy, h->stream);
+    if (err == cudaSuccess)
+        err = cudaStreamSynchronize(h->stream);
+    device_free(h->alloc, tmp);
+    if (err != cudaSuccess)
+        return cuda_fail(err, "lattice upload");
+    return sync_and_check(h);
+}
+
+int muca_set_attempt_counter(muca_t h, uint64_t t)
+{
+    int rc = validate(h);
+    if (rc)
+        return rc;
+    h->t = t;
+    return MUCA_OK;
+}
+
+int muca_save(muca_t h, const char *path)
+{
+    int rc = validate(h);
+    if (rc)
+        return rc;
+    if (!path)
+        return fail(MUCA_EINVAL, "NULL path");
+    const size_t N = (size_t)h->N, W = (size_t)h->W, nb = N + 1, row = (N + 7) / 8;
+    std::vector<uint64_t> H;
+    if ((rc = read_histogram(h, H)) != MUCA_OK)
+        return rc;
+    std::vector<int32_t> e(W);
+    if ((rc = muca_get_energies(h, e.data(), W)) != MUCA_OK)
+        return rc;
+    std::vector<int8_t> spins(W * N);
+    if ((rc = muca_get_lattice(h, spins.data(), spins.size())) != MUCA_OK)
+        return rc;
+    std::vector<uint8_t> bits(W * row, 0);
+    for (size_t w = 0; w < W; ++w)
+        for (size_t i = 0; i < N; ++i)
+            if (spins[w * N + i] < 0)
+                bits[w * row + i / 8] |= (uint8_t)(1u << (i % 8));
+    FileCloser fc{std::fopen(path, "wb")};
+    if (!fc.f)
+        return fail(MUCA_EIO, "cannot open %s for writing", path);
+    const int32_t L = h->L, layout = h->layout, wpb = h->wpb, order = h->order;
+    const int64_t nw = h->W;
+    const uint64_t seed = h->seed, t = h->t;
+    const bool ok = put(fc.f, kCheckpointMagic, 8) && put(fc.f, &L, 1) && put(fc.f, &layout, 1) &&
+                    put(fc.f, &nw, 1) && put(fc.f, &seed, 1) && put(fc.f, &wpb, 1) && put(fc.f, &order, 1) &&
+                    put(fc.f, &t, 1) && put(fc.f, h->lnW.data(), nb) && put(fc.f, H.data(), nb) &&
+                    put(fc.f, e.data(), W) && put(fc.f, bits.data(), bits.size());
+    if (!ok || std::fflush(fc.f) != 0)
+        return fail(MUCA_EIO, "writing %s failed", path);
+    return MUCA_OK;
+}
+
+int muca_load(const char *path, muca_t *out)
+{
+    if (!path || !out)
+        return fail(MUCA_EINVAL, "NULL argument");
+    *out = nullptr;
+    FileCloser fc{std::fopen(path, "rb")};
+    if (!fc.f)
+        return fail(MUCA_EIO, "cannot open %s", path);
+    char magic[8];
+    muca_options o;
+    std::memset(&o, 0, sizeof o);
+    int32_t order = 0;
+    uint64_t t = 0;
+    if (!get(fc.f, magic, 8) || std::memcmp(magic, kCheckpointMagic, 8) != 0)
+        return fail(MUCA_EIO, "%s is not a checkpoint of this library", path);
+    if (!get(fc.f, &o.L, 1) || !get(fc.f, &o.layout, 1) || !get(fc.f, &o.n_walkers, 1) || !get(fc.f, &o.seed, 1) ||
+        !get(fc.f, &o.walkers_per_block, 1) || !get(fc.f, &order, 1) || !get(fc.f, &t, 1))
+        return fail(MUCA_EIO, "%s: truncated header", path);
+    if (o.L < 4 || o.L > 64 || o.L % 4 != 0 || o.n_walkers < 1 || o.n_walkers > INT32_MAX ||
+        (o.layout != MUCA_LAYOUT_INT8 && o.layout != MUCA_LAYOUT_PACKED))
+        return fail(MUCA_EIO, "%s: invalid header", path);
+    const size_t N = (size_t)o.L * o.L, W = (size_t)o.n_walkers, nb = N + 1, row = (N + 7) / 8;
+    std::vector<double> lnW(nb);
+    std::vector<uint64_t> H(nb);
+    std::vector<int32_t> e(W);
+    std::vector<uint8_t> bits(W * row);
+    if (!get(fc.f, lnW.data(), nb) || !get(fc.f, H.data(), nb) || !get(fc.f, e.data(), W) ||
+        !get(fc.f, bits.data(), bits.size()))
+        return fail(MUCA_EIO, "%s: truncated", path);
+    std::vector<int8_t> spins(W * N);
+    for (size_t w = 0; w < W; ++w)
+        for (size_t i = 0; i < N; ++i)
+            spins[w * N + i] = ((bits[w * row + i / 8] >> (i % 8)) & 1u) ? (int8_t)-1 : (int8_t)1;
+    muca_t h = nullptr;
+    int rc = muca_create_ex(&o, &h);
+    if (rc)
+        return rc;
+    auto cleanup = [&](int code) {
+        muca_destroy(h);
+        return code;
+    };
+    if ((rc = muca_set_site_order(h, order)) != MUCA_OK || (rc = muca_set_weights(h, lnW.data(), nb)) != MUCA_OK ||
+        (rc = muca_set_lattice(h, spins.data(), spins.size())) != MUCA_OK)
+        return cleanup(rc);
+    std::vector<int32_t> e_now(W);
+    if ((rc = muca_get_energies(h, e_now.data(), W)) != MUCA_OK)
+        return cleanup(rc);
+    if (e_now != e)
+        return cleanup(fail(MUCA_EIO, "%s: stored energies do not match the stored lattices", path));
+    std::copy(H.begin(), H.end(), h->h_hist);
+    cudaError_t err = cudaMemcpyAsync(h->d_hist, h->h_hist, nb * sizeof(unsigned long long), cudaMemcpyHostToDevice,
+                                      h->stream);
+    if (err == cudaSuccess)
+        err = cudaStreamSynchronize(h->stream);
+    if (err != cudaSuccess)
+        return cleanup(cuda_fail(err, "histogram upload"));
+    h->t = t;
+    *out = h;
+    return MUCA_OK;
 }
 
 int muca_get_info(muca_t h, int32_t *L, int64_t *n_walkers, uint64_t *attempt_counter, int32_t *layout,

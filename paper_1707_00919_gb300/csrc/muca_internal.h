@@ -92,6 +92,10 @@ void set_full_kernel_enabled(bool on);
 cudaError_t launch_init(int32_t L, int32_t layout, int64_t W, uint64_t seed, void *lattice,
                         int32_t *energy, cudaStream_t s);
 
+// Packs lattices given as int8 in[walker][site] (+1/-1) and recomputes their energies.
+cudaError_t launch_pack(int32_t L, int32_t layout, int64_t W, const int8_t *in, void *lattice, int32_t *energy,
+                        cudaStream_t s);
+
 // Unpacks lattices into int8 out[walker][site] (+1/-1).
 cudaError_t launch_unpack(int32_t L, int32_t layout, int64_t W, const void *lattice, int8_t *out,
                           cudaStream_t s);

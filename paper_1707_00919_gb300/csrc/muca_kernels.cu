@@ -159,26 +159,17 @@ __global__ void __launch_bounds__(1024) sweep_kernel(const SweepArgs a)
 // Initial spins: +1 iff the top bit of the tag-1 word for attempt number t = site is
 // clear; the energy index is the number of unsatisfied bonds over two.
 // ---------------------------------------------------------------------------------
-template <typename RowT, int LAYOUT>
-__global__ void init_kernel(int32_t L, int64_t W, uint64_t seed, void *lattice, int32_t *energy)
+// Writes a walker's lattice, given row by row (bit x = spin at x is down), in the
+// instance's layout, and its energy index: the number of unsatisfied bonds over two.
+template <typename RowT, int LAYOUT, class RowSource>
+__device__ __forceinline__ void write_lattice(int32_t L, int64_t W, int64_t w, const RowSource &rows, void *lattice,
+                                              int32_t *energy)
 {
-    const int64_t w = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (w >= W)
-        return;
-    const uint32_t k0 = (uint32_t)seed, k1 = (uint32_t)(seed >> 32);
     const RowT mask = (L == (int)(8 * sizeof(RowT))) ? ~(RowT)0 : (((RowT)1 << L) - 1);
     RowT first = 0, prev = 0;
     int unsat = 0;
     for (int y = 0; y < L; ++y) {
-        RowT r = 0;
-        for (int x = 0; x < L; x += 4) {
-            const uint32_t site = (uint32_t)(y * L + x);
-            const uint4 q = philox4x32_10(make_uint4(site >> 2, 0u, (uint32_t)w, kTagInit), k0, k1);
-            const uint32_t words[4] = {q.x, q.y, q.z, q.w};
-#pragma unroll
-            for (int u = 0; u < 4; ++u)
-                r |= (RowT)(words[u] >> 31) << (x + u);
-        }
+        const RowT r = rows(y);
         const RowT rot = (r >> 1) | ((r & 1) << (L - 1));   // bit x = spin at x+1 (mod L)
         unsat += __popcll((unsigned long long)((r ^ rot) & mask));
         if (y == 0)
@@ -196,6 +187,59 @@ __global__ void init_kernel(int32_t L, int64_t W, uint64_t seed, void *lattice, 
     }
     unsat += __popcll((unsigned long long)((prev ^ first) & mask));   // row L-1 to row 0
     energy[w] = unsat / 2;
+}
+
+template <typename RowT>
+struct InitRows {
+    int32_t L;
+    uint32_t k0, k1, w;
+    __device__ RowT operator()(int y) const
+    {
+        RowT r = 0;
+        for (int x = 0; x < L; x += 4) {
+            const uint32_t site = (uint32_t)(y * L + x);
+            const uint4 q = philox4x32_10(make_uint4(site >> 2, 0u, w, kTagInit), k0, k1);
+            const uint32_t words[4] = {q.x, q.y, q.z, q.w};
+#pragma unroll
+            for (int u = 0; u < 4; ++u)
+                r |= (RowT)(words[u] >> 31) << (x + u);
+        }
+        return r;
+    }
+};
+
+template <typename RowT>
+struct GivenRows {
+    int32_t L;
+    const int8_t *spins;   // this walker's N spins, +1 / -1
+    __device__ RowT operator()(int y) const
+    {
+        RowT r = 0;
+        for (int x = 0; x < L; ++x)
+            r |= (RowT)(spins[y * L + x] < 0) << x;
+        return r;
+    }
+};
+
+template <typename RowT, int LAYOUT>
+__global__ void init_kernel(int32_t L, int64_t W, uint64_t seed, void *lattice, int32_t *energy)
+{
+    const int64_t w = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (w >= W)
+        return;
+    const InitRows<RowT> rows{L, (uint32_t)seed, (uint32_t)(seed >> 32), (uint32_t)w};
+    write_lattice<RowT, LAYOUT>(L, W, w, rows, lattice, energy);
+}
+
+// Lattices given as int8 in[walker][site] (+1 / -1) into the layout, energies recomputed.
+template <typename RowT, int LAYOUT>
+__global__ void pack_kernel(int32_t L, int64_t W, const int8_t *in, void *lattice, int32_t *energy)
+{
+    const int64_t w = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (w >= W)
+        return;
+    const GivenRows<RowT> rows{L, in + (size_t)w * (size_t)(L * L)};
+    write_lattice<RowT, LAYOUT>(L, W, w, rows, lattice, energy);
 }
 
 template <typename RowT, int LAYOUT>
@@ -334,6 +378,25 @@ cudaError_t launch_init(int32_t L, int32_t layout, int64_t W, uint64_t seed, voi
             init_kernel<unsigned long long, MUCA_LAYOUT_PACKED><<<blocks, threads, 0, s>>>(L, W, seed, lattice, energy);
         else
             init_kernel<unsigned long long, MUCA_LAYOUT_INT8><<<blocks, threads, 0, s>>>(L, W, seed, lattice, energy);
+    }
+    return cudaGetLastError();
+}
+
+cudaError_t launch_pack(int32_t L, int32_t layout, int64_t W, const int8_t *in, void *lattice, int32_t *energy,
+                        cudaStream_t s)
+{
+    const int threads = 128;
+    const unsigned blocks = (unsigned)((W + threads - 1) / threads);
+    if (L <= 32) {
+        if (layout == MUCA_LAYOUT_PACKED)
+            pack_kernel<uint32_t, MUCA_LAYOUT_PACKED><<<blocks, threads, 0, s>>>(L, W, in, lattice, energy);
+        else
+            pack_kernel<uint32_t, MUCA_LAYOUT_INT8><<<blocks, threads, 0, s>>>(L, W, in, lattice, energy);
+    } else {
+        if (layout == MUCA_LAYOUT_PACKED)
+            pack_kernel<unsigned long long, MUCA_LAYOUT_PACKED><<<blocks, threads, 0, s>>>(L, W, in, lattice, energy);
+        else
+            pack_kernel<unsigned long long, MUCA_LAYOUT_INT8><<<blocks, threads, 0, s>>>(L, W, in, lattice, energy);
     }
     return cudaGetLastError();
 }

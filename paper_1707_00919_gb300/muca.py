@@ -8,6 +8,7 @@ and, optionally, the CUDA stream the instance runs on.
 from __future__ import annotations
 
 import ctypes
+import os
 from dataclasses import dataclass
 
 import numpy as np
@@ -89,6 +90,25 @@ def muca_create_ex(L: int, n_walkers: int, seed: int, layout: int = MUCA_LAYOUT_
     o = muca_options(L, n_walkers, seed, layout, walkers_per_block)
     h = ctypes.c_void_p()
     _check(C.load().muca_create_ex(ctypes.byref(o), ctypes.byref(h)))
+    return h
+
+
+def muca_set_lattice(h, spins) -> None:
+    a = np.ascontiguousarray(spins, dtype=np.int8)
+    _check(C.load().muca_set_lattice(h, _p(a, ctypes.c_int8), a.size))
+
+
+def muca_set_attempt_counter(h, t: int) -> None:
+    _check(C.load().muca_set_attempt_counter(h, t))
+
+
+def muca_save(h, path: str) -> None:
+    _check(C.load().muca_save(h, os.fsencode(path)))
+
+
+def muca_load(path: str) -> ctypes.c_void_p:
+    h = ctypes.c_void_p()
+    _check(C.load().muca_load(os.fsencode(path), ctypes.byref(h)))
     return h
 
 
@@ -286,6 +306,30 @@ class Muca:
         if stream is not None:
             handle = getattr(stream, "cuda_stream", stream)
             muca_set_stream(self._h, int(handle))
+
+    @classmethod
+    def load(cls, path: str, stream=None, torch_allocator: bool = True) -> "Muca":
+        """An instance restored from a checkpoint written by save()."""
+        if torch_allocator:
+            use_torch_allocator()
+        self = cls.__new__(cls)
+        self._h = muca_load(path)
+        L, W, _, _, _ = muca_get_info(self._h)
+        self.L, self.N, self.W = L, L * L, W
+        self.n_bins = self.N + 1
+        if stream is not None:
+            muca_set_stream(self._h, int(getattr(stream, "cuda_stream", stream)))
+        return self
+
+    def save(self, path: str) -> None:
+        muca_save(self._h, path)
+
+    def set_lattice(self, spins) -> None:
+        """spins[walker][site], +1 / -1; energies are recomputed."""
+        muca_set_lattice(self._h, spins)
+
+    def set_attempt_counter(self, t: int) -> None:
+        muca_set_attempt_counter(self._h, t)
 
     # lifetime
     def close(self) -> None:

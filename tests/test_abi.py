@@ -55,6 +55,27 @@ def test_default_params_and_errors_without_gpu(lib):
     assert lib.muca_optimal_walkers(32, 0, None, None) == _lib.MUCA_EINVAL
 
 
+def test_checkpoint_files_are_checked_without_gpu(lib, tmp_path):
+    """muca_load reads and checks the file before it touches the device."""
+    import ctypes
+    from paper_1707_00919_gb300 import _lib
+    h = ctypes.c_void_p()
+    missing = str(tmp_path / "none.muca").encode()
+    assert lib.muca_load(missing, ctypes.byref(h)) == _lib.MUCA_EIO
+    junk = tmp_path / "junk.muca"
+    junk.write_bytes(b"NOTMUCA!" + bytes(64))
+    assert lib.muca_load(str(junk).encode(), ctypes.byref(h)) == _lib.MUCA_EIO
+    short = tmp_path / "short.muca"
+    short.write_bytes(b"MUCACKP1" + bytes(10))
+    assert lib.muca_load(str(short).encode(), ctypes.byref(h)) == _lib.MUCA_EIO
+    bad_l = tmp_path / "bad_l.muca"
+    import struct
+    bad_l.write_bytes(b"MUCACKP1" + struct.pack("<iiqQiiQ", 6, 0, 10, 1, 0, 0, 0))
+    assert lib.muca_load(str(bad_l).encode(), ctypes.byref(h)) == _lib.MUCA_EIO
+    assert lib.muca_load(None, ctypes.byref(h)) == _lib.MUCA_EINVAL
+    assert not h.value
+
+
 def test_missing_library_fails_loudly(monkeypatch, tmp_path):
     from paper_1707_00919_gb300 import _lib
     monkeypatch.setattr(_lib, "LIB_PATH", str(tmp_path / "nope.so"))
