@@ -7,7 +7,6 @@
 // One thread runs one walker; its lattice sits in shared memory as one bit row per
 // lattice row ([row][walker-in-block]); the block draws the sites of a chunk of
 // attempts into shared memory together, then every walker runs the chunk.
-#include <algorithm>
 #include <cstdint>
 
 #include "muca_device.cuh"
