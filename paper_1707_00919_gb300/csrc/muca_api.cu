@@ -209,7 +209,7 @@ int run_attempts(muca_t h, uint64_t n, bool record, const uint32_t *skip = nullp
         a.err = h->d_err;
         a.skip = skip;
         if (h->order == MUCA_ORDER_RANDOM)
-            MUCA_CUDA(muca::launch_random_sweep(a, record, h->stream), "random-order sweep launch");
+            MUCA_CUDA(muca::launch_random_sweep(a, h->wpb, record, h->stream), "random-order sweep launch");
         else
             MUCA_CUDA(muca::launch_sweep(a, h->wpb, record, h->stream), "sweep launch");
         h->t += chunk;

@@ -80,8 +80,9 @@ size_t sweep_smem_limit();
 cudaError_t launch_sweep(const SweepArgs &a, int walkers_per_block, bool record, cudaStream_t s);
 
 // Runs attempts [t0, t0 + n) of every walker in random shared site order (muca_random.cu;
-// any L, any attempt range; its own block size, chosen to fit shared memory).
-cudaError_t launch_random_sweep(const SweepArgs &a, bool record, cudaStream_t s);
+// any L, any attempt range; the given block size, or a smaller one that fits shared
+// memory).
+cudaError_t launch_random_sweep(const SweepArgs &a, int walkers_per_block, bool record, cudaStream_t s);
 size_t random_smem_bytes(int L, int walkers_per_block, bool record);
 
 // Routes whole sweeps to the generic kernel when false (used by tests that compare the

@@ -58,7 +58,8 @@ __global__ void __launch_bounds__(1024) sweep_kernel(const SweepArgs a)
             const int8_t *g = reinterpret_cast<const int8_t *>(a.lattice);
             for (int y = 0; y < L; ++y) {
                 RowT r = 0;
-                for (int x = 0; x < L; ++x)
+#pragma unroll 16
+                for (int x = 0; x < L; ++x)   // unrolled: a row's loads are in flight together
                     r |= (RowT)(g[(size_t)(y * L + x) * a.W + w] < 0) << x;
                 col[y * wpb] = r;
             }

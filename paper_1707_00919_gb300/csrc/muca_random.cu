@@ -20,7 +20,7 @@ template <typename RowT>
 size_t random_smem_bytes_t(int L, int wpb, bool record)
 {
     const size_t nb = (size_t)L * L + 1;
-    return align_up((nb * 5 + (record ? nb : 0)) * 4 + (size_t)kSiteChunk * 2, 16) + (size_t)L * wpb * sizeof(RowT);
+    return align_up((nb * 5 + (record ? nb : 0)) * 4, 16) + (size_t)kSiteChunk * 16 + (size_t)L * wpb * sizeof(RowT);
 }
 
 template <typename RowT, int LAYOUT, bool RECORD>
@@ -35,9 +35,10 @@ __global__ void __launch_bounds__(256) random_sweep_kernel(const SweepArgs a)
     const int wpb = blockDim.x;
     uint32_t *sT = reinterpret_cast<uint32_t *>(smem);
     uint32_t *sH = sT + nb * 5;
-    uint16_t *sSite = reinterpret_cast<uint16_t *>(sH + (RECORD ? nb : 0));
-    RowT *sRows = reinterpret_cast<RowT *>(smem + align_up((size_t)(nb * 5 + (RECORD ? nb : 0)) * 4 +
-                                                               (size_t)kSiteChunk * 2, 16));
+    // per site of the chunk: row offsets (row * wpb) of the rows above, at and below,
+    // and x | x_left << 8 | x_right << 16; shared by all walkers of the block
+    uint4 *sSite = reinterpret_cast<uint4 *>(smem + align_up((size_t)(nb * 5 + (RECORD ? nb : 0)) * 4, 16));
+    RowT *sRows = reinterpret_cast<RowT *>(reinterpret_cast<unsigned char *>(sSite) + (size_t)kSiteChunk * 16);
     const int tid = threadIdx.x;
     const int64_t w = (int64_t)blockIdx.x * wpb + tid;
     bool active = w < a.W;
@@ -58,7 +59,8 @@ __global__ void __launch_bounds__(256) random_sweep_kernel(const SweepArgs a)
             const int8_t *g = reinterpret_cast<const int8_t *>(a.lattice);
             for (int y = 0; y < L; ++y) {
                 RowT r = 0;
-                for (int x = 0; x < L; ++x)
+#pragma unroll 16
+                for (int x = 0; x < L; ++x)   // unrolled: a row's loads are in flight together
                     r |= (RowT)(g[(size_t)(y * L + x) * a.W + w] < 0) << x;
                 col[y * wpb] = r;
             }
@@ -72,8 +74,6 @@ __global__ void __launch_bounds__(256) random_sweep_kernel(const SweepArgs a)
     const uint32_t k0 = (uint32_t)a.seed, k1 = (uint32_t)(a.seed >> 32);
     const uint32_t wid = (uint32_t)w;
     const uint64_t tend = a.t0 + a.n;
-    uint64_t cached = ~0ull;
-    uint4 words = make_uint4(0u, 0u, 0u, 0u);
     for (uint64_t tc = a.t0; tc < tend; tc += kSiteChunk) {
         const int m = tend - tc < (uint64_t)kSiteChunk ? (int)(tend - tc) : kSiteChunk;
         __syncthreads();   // the previous chunk's sites are consumed (and the setup done)
@@ -84,37 +84,76 @@ __global__ void __launch_bounds__(256) random_sweep_kernel(const SweepArgs a)
                                           k0, k1);
             const uint32_t u = (t & 3) == 0 ? q.x : (t & 3) == 1 ? q.y : (t & 3) == 2 ? q.z : q.w;
             const uint32_t i = __umulhi(u, (uint32_t)N);
-            const uint32_t y = i / (uint32_t)L;
-            sSite[j] = (uint16_t)((y << 8) | (i - y * (uint32_t)L));
+            const int y = (int)(i / (uint32_t)L), x = (int)i - y * L;
+            const int yu = (y == 0) ? L - 1 : y - 1, yd = (y == L - 1) ? 0 : y + 1;
+            const int xl = (x == 0) ? L - 1 : x - 1, xr = (x == L - 1) ? 0 : x + 1;
+            sSite[j] = make_uint4((uint32_t)(yu * wpb), (uint32_t)(y * wpb), (uint32_t)(yd * wpb),
+                                  (uint32_t)(x | (xl << 8) | (xr << 16)));
         }
         __syncthreads();
         if (!active)
             continue;
-        for (int j = 0; j < m; ++j) {
-            const uint64_t t = tc + (uint64_t)j;
-            if ((t >> 2) != cached) {
-                cached = t >> 2;
-                words = philox4x32_10(make_uint4((uint32_t)cached, (uint32_t)(cached >> 32), wid, kTagMetropolis),
-                                      k0, k1);
+        // The rows of the next attempt's site are loaded before the current attempt
+        // decides (its flip is then applied to them where the rows coincide), which
+        // takes the row loads off the attempt-to-attempt chain (energy, threshold
+        // load, compare).
+        uint4 site = sSite[0];
+        RowT U = col[site.x], C = col[site.y], D = col[site.z];
+        bool pacc = false;
+        uint32_t prow = 0xFFFFFFFFu;   // row offset of the previous attempt's site
+        RowT pbit = 0;
+        int j = 0;
+        uint64_t t = tc;
+        auto attempt = [&](uint32_t r) {
+            if (pacc) {   // the previous attempt flipped a site after these rows were read
+                U ^= (site.x == prow) ? pbit : (RowT)0;
+                C ^= (site.y == prow) ? pbit : (RowT)0;
+                D ^= (site.z == prow) ? pbit : (RowT)0;
             }
-            const uint32_t r = (t & 3) == 0 ? words.x : (t & 3) == 1 ? words.y : (t & 3) == 2 ? words.z : words.w;
-            const uint32_t p = sSite[j];
-            const int y = (int)(p >> 8), x = (int)(p & 0xFFu);
-            const int yu = (y == 0) ? L - 1 : y - 1;
-            const int yd = (y == L - 1) ? 0 : y + 1;
-            const int xl = (x == 0) ? L - 1 : x - 1;
-            const int xr = (x == L - 1) ? 0 : x + 1;
-            const RowT C = col[y * wpb];
+            uint4 nsite = site;
+            RowT nU = 0, nC = 0, nD = 0;
+            if (j + 1 < m) {
+                nsite = sSite[j + 1];
+                nU = col[nsite.x];
+                nC = col[nsite.y];
+                nD = col[nsite.z];
+            }
+            const int x = (int)(site.w & 0xFFu), xl = (int)((site.w >> 8) & 0xFFu), xr = (int)(site.w >> 16);
             const uint32_t sx = bit_at(C, x);
-            const uint32_t k = (sx ^ bit_at(col[yu * wpb], x)) + (sx ^ bit_at(col[yd * wpb], x)) +
-                               (sx ^ bit_at(C, xl)) + (sx ^ bit_at(C, xr));
+            const uint32_t k = (sx ^ bit_at(U, x)) + (sx ^ bit_at(D, x)) + (sx ^ bit_at(C, xl)) + (sx ^ bit_at(C, xr));
             const uint32_t thr = sT[e * 5 + (int)k];
-            if (r < thr || thr == 0xFFFFFFFFu) {
-                col[y * wpb] = C ^ ((RowT)1 << x);
+            const bool acc = r < thr || thr == 0xFFFFFFFFu;
+            const RowT bx = (RowT)1 << x;
+            if (acc) {
+                col[site.y] = C ^ bx;
                 e += 2 - (int)k;
             }
             if (RECORD)
                 atomicAdd(&sH[e], 1u);
+            pacc = acc;
+            prow = site.y;
+            pbit = bx;
+            site = nsite;
+            U = nU;
+            C = nC;
+            D = nD;
+            ++j;
+            ++t;
+        };
+        while (j < m) {
+            // one Philox call serves the attempts of its block (t & 3 = 0 .. 3)
+            const uint64_t blk = t >> 2;
+            const uint4 rw = philox4x32_10(make_uint4((uint32_t)blk, (uint32_t)(blk >> 32), wid, kTagMetropolis),
+                                           k0, k1);
+            const int u0 = (int)(t & 3);
+            if (u0 <= 0 && j < m)
+                attempt(rw.x);
+            if (u0 <= 1 && j < m)
+                attempt(rw.y);
+            if (u0 <= 2 && j < m)
+                attempt(rw.z);
+            if (j < m)
+                attempt(rw.w);
         }
     }
     __syncthreads();
@@ -174,14 +213,15 @@ size_t random_smem_bytes(int L, int wpb, bool record)
                    : random_smem_bytes_t<unsigned long long>(L, wpb, record);
 }
 
-cudaError_t launch_random_sweep(const SweepArgs &a, bool record, cudaStream_t s)
+cudaError_t launch_random_sweep(const SweepArgs &a, int walkers_per_block, bool record, cudaStream_t s)
 {
     if (a.n == 0 || a.W == 0)
         return cudaSuccess;
-    // the largest block of whole warps whose rows fit next to the table, histogram and
-    // site buffer (the walker-to-thread mapping does not affect the result)
+    // the instance's block size (one warp per SM sub-partition where the walker count
+    // allows), else the largest block of whole warps whose rows fit next to the table,
+    // histogram and site buffer (the walker-to-thread mapping does not affect the result)
     const size_t limit = sweep_smem_limit();
-    int wpb = 256;
+    int wpb = walkers_per_block >= 32 && walkers_per_block <= 256 ? walkers_per_block : 256;
     while (wpb > 32 && random_smem_bytes(a.L, wpb, record) > limit)
         wpb -= 32;
     if (random_smem_bytes(a.L, wpb, record) > limit)
