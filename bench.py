@@ -179,9 +179,9 @@ class ClockSampler:
         return {"sm_mhz": sm[len(sm) // 2], "sm_max_mhz": mx, "reasons": sorted(reasons), "samples": len(sm)}
 
 
-# Sources that define the timed whole-sweep kernel at L = 32 (body, launcher, constants).
+# Sources that define the timed whole-sweep kernel at L = 32 (body and launcher).
 KERNEL_SOURCES = [os.path.join(ROOT, "paper_1707_00919_gb300", "csrc", f)
-                  for f in ("muca_device.cuh", "muca_full.cuh", "muca_full_32.cu", "muca_internal.h")]
+                  for f in ("muca_device.cuh", "muca_full.cuh", "muca_full_32.cu")]
 TRAFFIC_PROFILE = os.path.join(ROOT, "profiles", "sweep_full_kernel_L32_W16384_int8.md")
 
 
@@ -376,6 +376,11 @@ def run_native(args):
     rec_attempts = WALKERS * SWEEPS_PER_ITER * N
     achieved_tops = OPS_PER_ATTEMPT * rec_attempts / rec_launch_s / 1e12
     traffic = profiled_traffic()
+    # measured issue rates of the instruction classes the sweep uses (context for the peak)
+    probe = {name: M.muca_measure_issue_rate(kind) / 1e12
+             for name, kind in (("xor3_alu", M.MUCA_PROBE_XOR), ("imad", M.MUCA_PROBE_MAD),
+                                ("xor3_imad_alternating", M.MUCA_PROBE_MIXED))}
+    philox_words = M.muca_measure_issue_rate(M.MUCA_PROBE_PHILOX)
     result = {
         "metric": "spin-flip attempts/s (and time-to-flat H) at L=32, 16384 walkers; % of integer-issue roofline",
         "value": value,
@@ -405,7 +410,9 @@ def run_native(args):
                      "frac": achieved_tops / peak_tops, "traffic": traffic,
                      "kernel": "sweep_full_kernel<32,int8,record>",
                      "ops_per_attempt": OPS_PER_ATTEMPT,
-                     "peak_basis": f"{sm_count} SMs x 4 issue slots x 32 lanes x {sm_max_mhz:.0f} MHz"},
+                     "peak_basis": f"{sm_count} SMs x 4 issue slots x 32 lanes x {sm_max_mhz:.0f} MHz",
+                     "measured_issue_tops": {k: round(v, 3) for k, v in probe.items()},
+                     "measured_philox_words_per_s": philox_words},
         "clocks": clocks.summary(),
     }
     m.close()

@@ -177,6 +177,21 @@ int muca_set_attempt_counter(muca_t h, uint64_t t);
 int muca_save(muca_t h, const char *path);
 int muca_load(const char *path, muca_t *out);
 
+/* Measurement helper (no counterpart in the paper): the rate at which the current
+ * device issues one integer instruction class when every SM sub-partition has 16 warps
+ * of independent work, for the integer roofline of the sweep kernels.  kind:
+ * MUCA_PROBE_XOR (three-input XOR: the integer ALU pipe), MUCA_PROBE_MAD (32-bit
+ * multiply-add), MUCA_PROBE_MIXED (the two alternating), MUCA_PROBE_PHILOX
+ * (Philox4x32-10 words, Sec. 2.3's generator).  *per_second receives thread
+ * instructions per second (words per second for MUCA_PROBE_PHILOX).  Runs for about
+ * 0.1 s; allocates 4 KiB of device memory.  Errors: MUCA_EINVAL (unknown kind, NULL),
+ * MUCA_ECUDA. */
+#define MUCA_PROBE_XOR 0
+#define MUCA_PROBE_MAD 1
+#define MUCA_PROBE_MIXED 2
+#define MUCA_PROBE_PHILOX 3
+int muca_measure_issue_rate(int32_t kind, double *per_second);
+
 /* Site order of later updates (sweeps, attempts, iterations, production):
  * MUCA_ORDER_TYPEWRITER (default): attempt t flips site t mod N;
  * MUCA_ORDER_RANDOM: the paper's scheme (Sec. 2.3), one random site sequence shared by

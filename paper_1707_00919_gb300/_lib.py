@@ -28,6 +28,10 @@ MUCA_WPB_TUNE = -1
 MUCA_WALKERS_OPTIMAL = -1
 MUCA_ORDER_TYPEWRITER = 0
 MUCA_ORDER_RANDOM = 1
+MUCA_PROBE_XOR = 0
+MUCA_PROBE_MAD = 1
+MUCA_PROBE_MIXED = 2
+MUCA_PROBE_PHILOX = 3
 
 MUCA_STOP_MIN_MEAN = 0
 MUCA_STOP_KL = 1
@@ -94,6 +98,7 @@ SIGNATURES = {
     "muca_optimal_walkers": (ctypes.c_int, [ctypes.c_int32, ctypes.c_int32, _P(ctypes.c_int64), _P(ctypes.c_int32)]),
     "muca_iterate_device": (ctypes.c_int, [_H, _P(muca_params), ctypes.c_int32, _P(muca_stats)]),
     "muca_set_site_order": (ctypes.c_int, [_H, ctypes.c_int32]),
+    "muca_measure_issue_rate": (ctypes.c_int, [ctypes.c_int32, _P(ctypes.c_double)]),
     "muca_set_lattice": (ctypes.c_int, [_H, _P(ctypes.c_int8), ctypes.c_size_t]),
     "muca_set_attempt_counter": (ctypes.c_int, [_H, ctypes.c_uint64]),
     "muca_save": (ctypes.c_int, [_H, ctypes.c_char_p]),

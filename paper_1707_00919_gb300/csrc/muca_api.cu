@@ -879,6 +879,16 @@ int muca_destroy(muca_t h)
     return MUCA_OK;
 }
 
+int muca_measure_issue_rate(int32_t kind, double *per_second)
+{
+    if (!per_second)
+        return fail(MUCA_EINVAL, "NULL argument");
+    if (kind < MUCA_PROBE_XOR || kind > MUCA_PROBE_PHILOX)
+        return fail(MUCA_EINVAL, "unknown probe kind %d", kind);
+    MUCA_CUDA(muca::measure_issue_rate(kind, per_second), "issue-rate probe");
+    return MUCA_OK;
+}
+
 int muca_set_site_order(muca_t h, int32_t order)
 {
     int rc = validate(h);

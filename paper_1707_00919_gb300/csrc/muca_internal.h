@@ -145,6 +145,9 @@ static_assert(kNoAllocCounterOffset + sizeof(uint32_t) <= kNoAllocScratchBytes, 
 cudaError_t launch_batch_noalloc(const SweepArgs *descs, const int32_t *wpbs, int32_t n, size_t smem, bool record,
                                  cudaStream_t s);
 
+// Issue rate of one instruction class (muca_probe.cu, see muca_measure_issue_rate).
+cudaError_t measure_issue_rate(int kind, double *per_second);
+
 // Bytes of the lattice storage of W walkers.
 size_t lattice_bytes(int32_t L, int32_t layout, int64_t W);
 

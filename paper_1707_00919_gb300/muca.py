@@ -15,7 +15,8 @@ import numpy as np
 
 from . import _lib as C
 from ._lib import (MUCA_LAYOUT_AUTO, MUCA_LAYOUT_INT8, MUCA_LAYOUT_PACKED, MUCA_OK,  # noqa: F401
-                   MUCA_ORDER_RANDOM, MUCA_ORDER_TYPEWRITER, MUCA_SCHEDULE_PAPER, MUCA_WALKERS_OPTIMAL,
+                   MUCA_ORDER_RANDOM, MUCA_ORDER_TYPEWRITER, MUCA_PROBE_MAD, MUCA_PROBE_MIXED,
+                   MUCA_PROBE_PHILOX, MUCA_PROBE_XOR, MUCA_SCHEDULE_PAPER, MUCA_WALKERS_OPTIMAL,
                    MUCA_WPB_TUNE,
                    MUCA_SCHEDULE_SWEEPS, MUCA_STOP_CHEBYSHEV, MUCA_STOP_KL, MUCA_STOP_MIN_MEAN,
                    muca_options, muca_params, muca_stats)
@@ -110,6 +111,12 @@ def muca_load(path: str) -> ctypes.c_void_p:
     h = ctypes.c_void_p()
     _check(C.load().muca_load(os.fsencode(path), ctypes.byref(h)))
     return h
+
+
+def muca_measure_issue_rate(kind: int) -> float:
+    v = ctypes.c_double()
+    _check(C.load().muca_measure_issue_rate(kind, ctypes.byref(v)))
+    return v.value
 
 
 def muca_set_site_order(h, order: int) -> None:

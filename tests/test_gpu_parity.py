@@ -264,3 +264,19 @@ def test_optimal_walkers(muca_mod, orc, L):
         s, eo = orc.init(L, 5, 1, walker0=w)
         orc.run(L, 5, s, eo, T, 0, N, False, None, walker0=w)
         assert np.array_equal(lat[w], s[0]) and e[w] == eo[0] == e_index(L, lat[w])
+
+
+def test_issue_rate_probe(muca_mod):
+    """The integer issue rates the roofline rests on: every class positive and below the
+    issue-slot ceiling (SMs x 4 x 32 lanes x the maximum clock); unknown kinds refused."""
+    import torch
+    M = muca_mod
+    props = torch.cuda.get_device_properties(0)
+    ceiling = props.multi_processor_count * 4 * 32 * 2.2e9
+    rates = {k: M.muca_measure_issue_rate(k) for k in (M.MUCA_PROBE_XOR, M.MUCA_PROBE_MAD, M.MUCA_PROBE_MIXED)}
+    for r in rates.values():
+        assert 0.05 * ceiling < r < 1.05 * ceiling
+    words = M.muca_measure_issue_rate(M.MUCA_PROBE_PHILOX)
+    assert 1e11 < words < ceiling
+    with pytest.raises(M.MucaError):
+        M.muca_measure_issue_rate(9)
