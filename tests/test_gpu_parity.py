@@ -280,3 +280,29 @@ def test_issue_rate_probe(muca_mod):
     assert 1e11 < words < ceiling
     with pytest.raises(M.MucaError):
         M.muca_measure_issue_rate(9)
+
+
+@pytest.mark.parametrize("L,W,layout", [(8, 1, 0), (32, 1, 1), (64, 1, 0), (16, 16, 0), (16, 32, 0), (16, 33, 0),
+                                        (24, 48, 1)])
+def test_edge_walker_counts_and_empty_launches(muca_mod, orc, L, W, layout):
+    """A single walker, half and whole warps, one walker past a warp; launches of zero
+    sweeps or attempts change nothing (the counter included)."""
+    M = muca_mod
+    N = L * L
+    lnW = rand_weights(L, 7, 0.1)
+    with M.Muca(L, W, 31, layout=layout) as m:
+        m.set_weights(lnW)
+        m.sweep(0, True)
+        m.attempts(0, True)
+        assert m.info()[2] == 0 and int(m.get_histogram().sum()) == 0
+        m.sweep(2, False)
+        m.reset_histogram()
+        m.attempts(N + 7, True)
+        m.sweep(0, False)
+        lat, e, H, t = m.get_lattice(), m.get_energies(), m.get_histogram(), m.info()[2]
+    s, eo = orc.init(L, 31, W)
+    T = orc.build_table(L, lnW)
+    orc.run(L, 31, s, eo, T, 0, 2 * N, False)
+    Ho = orc.run(L, 31, s, eo, T, 2 * N, N + 7, True)
+    assert t == 3 * N + 7
+    assert np.array_equal(lat, s) and np.array_equal(e, eo) and np.array_equal(H, Ho)
