@@ -102,6 +102,10 @@ typedef struct {
     int32_t layout;              /* MUCA_LAYOUT_* (AUTO: measured choice)                   */
     int32_t walkers_per_block;   /* 0 = from occupancy, MUCA_WPB_TUNE = measured, else a
                                     multiple of 32 in [32, 256]                            */
+    int64_t first_walker;        /* global index of this instance's walker 0 (default 0):
+                                    instances holding disjoint walker ranges of one
+                                    simulation draw the random numbers of one instance
+                                    holding them all; first_walker + n_walkers <= 2^31    */
 } muca_options;
 
 /* Parameters of muca_iterate_until_flat.  muca_default_params fills the paper's values
@@ -165,6 +169,7 @@ int muca_destroy(muca_t h);
  * muca_set_attempt_counter: sets t, the counter of the next attempt.
  * muca_save: writes the state and the creation options to a binary file (little-endian:
  * 8-byte magic "MUCACKP1", L, layout, n_walkers, seed, walkers_per_block, site order, t,
+ * first_walker,
  * ln W[N+1] FP64, H[N+1] uint64, energies int32[n_walkers], then per walker N bits,
  * rounded up to whole bytes, bit i of byte i/8 set for a down spin at site i).
  * muca_load: creates an instance from such a file (same options) and restores the state;
@@ -218,6 +223,20 @@ int muca_set_allocator(void *(*alloc)(size_t size, void *ctx), void (*release)(v
  * acceptance-threshold table (Sec. 2.3).  Errors: MUCA_EINVAL (wrong n_bins, NULL,
  * non-finite value). */
 int muca_set_weights(muca_t h, const double *lnW, size_t n_bins);
+
+/* Histogram reduction for a simulation spread over several instances (Sec. 2.2: the
+ * walkers' histograms are summed before the weights are updated), e.g. one instance per
+ * GPU with disjoint walker ranges (muca_options.first_walker).  fn(H, n_bins, ctx) is
+ * called on the host with the instance's histogram after every recorded phase of
+ * muca_iterate_until_flat, muca_production and muca_production_jackknife, before it is
+ * used, and must replace it by the sum over all instances of the simulation (an
+ * all-reduce); every instance then takes the same stop decision and computes the same
+ * weights.  total_walkers (>= n_walkers) is the simulation's walker count, used by the
+ * Eq. (7) schedule.  fn == NULL removes it.  muca_get_histogram still returns the
+ * instance's own counts.  muca_iterate_device and muca_batch_create refuse instances
+ * with a reducer (MUCA_EINVAL). */
+typedef void (*muca_histogram_reducer)(uint64_t *H, size_t n_bins, void *ctx);
+int muca_set_histogram_reducer(muca_t h, muca_histogram_reducer fn, void *ctx, int64_t total_walkers);
 
 /* Copies the current ln W into lnW_out[n_bins]. */
 int muca_get_weights(muca_t h, double *lnW_out, size_t n_bins);

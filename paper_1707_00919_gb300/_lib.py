@@ -43,7 +43,8 @@ MUCA_SCHEDULE_PAPER = 1
 
 class muca_options(ctypes.Structure):
     _fields_ = [("L", ctypes.c_int32), ("n_walkers", ctypes.c_int64), ("seed", ctypes.c_uint64),
-                ("layout", ctypes.c_int32), ("walkers_per_block", ctypes.c_int32)]
+                ("layout", ctypes.c_int32), ("walkers_per_block", ctypes.c_int32),
+                ("first_walker", ctypes.c_int64)]
 
 
 class muca_params(ctypes.Structure):
@@ -90,6 +91,8 @@ RELEASE_FN = ctypes.CFUNCTYPE(None, ctypes.c_void_p, ctypes.c_void_p)
 
 # name -> (restype, argtypes), the symbols of include/muca.h
 _P = ctypes.POINTER
+# muca_histogram_reducer: void (*)(uint64_t *H, size_t n_bins, void *ctx)
+REDUCER = ctypes.CFUNCTYPE(None, ctypes.POINTER(ctypes.c_uint64), ctypes.c_size_t, ctypes.c_void_p)
 _H = ctypes.c_void_p
 SIGNATURES = {
     "muca_default_params": (ctypes.c_int, [_P(muca_params)]),
@@ -98,6 +101,7 @@ SIGNATURES = {
     "muca_optimal_walkers": (ctypes.c_int, [ctypes.c_int32, ctypes.c_int32, _P(ctypes.c_int64), _P(ctypes.c_int32)]),
     "muca_iterate_device": (ctypes.c_int, [_H, _P(muca_params), ctypes.c_int32, _P(muca_stats)]),
     "muca_set_site_order": (ctypes.c_int, [_H, ctypes.c_int32]),
+    "muca_set_histogram_reducer": (ctypes.c_int, [_H, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int64]),
     "muca_measure_issue_rate": (ctypes.c_int, [ctypes.c_int32, _P(ctypes.c_double)]),
     "muca_set_lattice": (ctypes.c_int, [_H, _P(ctypes.c_int8), ctypes.c_size_t]),
     "muca_set_attempt_counter": (ctypes.c_int, [_H, ctypes.c_uint64]),

@@ -116,6 +116,10 @@ struct muca_s {
     muca::IterState *h_iter = nullptr;   // pinned staging of the state
     uint64_t t = 0;                  // attempt counter (tag 0 stream)
     int32_t order = MUCA_ORDER_TYPEWRITER;   // site order of the updates
+    uint32_t walker0 = 0;            // global index of walker 0
+    muca_histogram_reducer reducer = nullptr;   // sum over the instances of one simulation
+    void *reducer_ctx = nullptr;
+    int64_t total_walkers = 0;       // walkers of the whole simulation (Eq. (7)), 0 = W
     int32_t kl_lo = -1, kl_hi = -1;  // range visited in the previous batched iteration
 };
 
@@ -208,6 +212,7 @@ int run_attempts(muca_t h, uint64_t n, bool record, const uint32_t *skip = nullp
         a.hist = h->d_hist;
         a.err = h->d_err;
         a.skip = skip;
+        a.walker0 = h->walker0;
         if (h->order == MUCA_ORDER_RANDOM)
             MUCA_CUDA(muca::launch_random_sweep(a, h->wpb, record, h->stream), "random-order sweep launch");
         else
@@ -229,6 +234,16 @@ int read_histogram(muca_t h, std::vector<uint64_t> &H)
         return rc;
     H.assign(h->h_hist, h->h_hist + nb);
     return MUCA_OK;
+}
+
+// The histogram as the iteration and the production use it: the instance's own, or its
+// sum over all instances of the simulation when a reducer is set.
+int read_reduced_histogram(muca_t h, std::vector<uint64_t> &H)
+{
+    const int rc = read_histogram(h, H);
+    if (rc == MUCA_OK && h->reducer)
+        h->reducer(H.data(), H.size(), h->reducer_ctx);
+    return rc;
 }
 
 // ---------------------------------------------------------------------------------
@@ -468,6 +483,7 @@ muca::SweepArgs make_args(muca_t h, uint64_t t0, uint64_t n)
     a.layout = h->layout;
     a.W = h->W;
     a.seed = h->seed;
+    a.walker0 = h->walker0;
     a.t0 = t0;
     a.n = n;
     a.lattice = h->d_lattice;
@@ -766,6 +782,9 @@ int muca_create_ex(const muca_options *opt, muca_t *out)
     }
     if (opt->n_walkers < 1 || opt->n_walkers > INT32_MAX)
         return fail(MUCA_EINVAL, "n_walkers = %lld out of range", (long long)opt->n_walkers);
+    if (opt->first_walker < 0 || opt->first_walker > (int64_t)INT32_MAX - opt->n_walkers)
+        return fail(MUCA_EINVAL, "first_walker = %lld: the walker indices must stay below 2^31",
+                    (long long)opt->first_walker);
     if (opt->layout != MUCA_LAYOUT_INT8 && opt->layout != MUCA_LAYOUT_PACKED && opt->layout != MUCA_LAYOUT_AUTO)
         return fail(MUCA_EINVAL, "unknown layout %d", opt->layout);
     if (opt->layout == MUCA_LAYOUT_AUTO || opt->walkers_per_block == MUCA_WPB_TUNE) {
@@ -792,6 +811,7 @@ int muca_create_ex(const muca_options *opt, muca_t *out)
     h->N = L * L;
     h->W = opt->n_walkers;
     h->seed = opt->seed;
+    h->walker0 = (uint32_t)opt->first_walker;
     h->layout = opt->layout;
     h->wpb = wpb;
     {
@@ -842,7 +862,7 @@ int muca_create_ex(const muca_options *opt, muca_t *out)
         err = cudaMemsetAsync(h->d_err, 0, sizeof(uint32_t), h->stream);
     if (err != cudaSuccess)
         return cleanup(cuda_fail(err, "memset"));
-    err = muca::launch_init(L, h->layout, h->W, h->seed, h->d_lattice, h->d_energy, h->stream);
+    err = muca::launch_init(L, h->layout, h->W, h->seed, h->walker0, h->d_lattice, h->d_energy, h->stream);
     if (err != cudaSuccess)
         return cleanup(cuda_fail(err, "init launch"));
     int rc = upload_table(h);
@@ -886,6 +906,20 @@ int muca_measure_issue_rate(int32_t kind, double *per_second)
     if (kind < MUCA_PROBE_XOR || kind > MUCA_PROBE_PHILOX)
         return fail(MUCA_EINVAL, "unknown probe kind %d", kind);
     MUCA_CUDA(muca::measure_issue_rate(kind, per_second), "issue-rate probe");
+    return MUCA_OK;
+}
+
+int muca_set_histogram_reducer(muca_t h, muca_histogram_reducer fn, void *ctx, int64_t total_walkers)
+{
+    int rc = validate(h);
+    if (rc)
+        return rc;
+    if (fn && total_walkers < h->W)
+        return fail(MUCA_EINVAL, "total_walkers = %lld is below this instance's %lld walkers",
+                    (long long)total_walkers, (long long)h->W);
+    h->reducer = fn;
+    h->reducer_ctx = fn ? ctx : nullptr;
+    h->total_walkers = fn ? total_walkers : 0;
     return MUCA_OK;
 }
 
@@ -1041,7 +1075,8 @@ int muca_iterate_until_flat(muca_t h, const muca_params *p_in, muca_stats *stats
             if (full) {
                 n_upd = (uint64_t)std::floor(p.growth * (double)upd_prev) + 1u;
             } else {
-                n_upd = (uint64_t)std::floor(p.factor * std::pow((double)w, p.z) / (double)h->W) + 1u;
+                const double walkers = (double)(h->total_walkers > 0 ? h->total_walkers : h->W);
+                n_upd = (uint64_t)std::floor(p.factor * std::pow((double)w, p.z) / walkers) + 1u;
                 full = prev_width == N + 1;
             }
         }
@@ -1057,7 +1092,7 @@ int muca_iterate_until_flat(muca_t h, const muca_params *p_in, muca_stats *stats
         rc = run_attempts(h, n_upd, true);
         if (rc)
             return rc;
-        rc = read_histogram(h, H);
+        rc = read_reduced_histogram(h, H);
         if (rc)
             return rc;
         spent += n_therm + n_upd;
@@ -1148,6 +1183,8 @@ int muca_iterate_device(muca_t h, const muca_params *p_in, int32_t iterations_pe
         muca_default_params(&p);
     if (p.schedule != MUCA_SCHEDULE_SWEEPS)
         return fail(MUCA_EINVAL, "muca_iterate_device runs the fixed-sweep schedule only");
+    if (h->reducer)
+        return fail(MUCA_EINVAL, "muca_iterate_device cannot reduce histograms over instances");
     if (p.stop_rule < MUCA_STOP_MIN_MEAN || p.stop_rule > MUCA_STOP_CHEBYSHEV)
         return fail(MUCA_EINVAL, "unknown stop rule %d", p.stop_rule);
     if (p.max_iterations < 1)
@@ -1255,7 +1292,7 @@ int muca_production(muca_t h, uint64_t therm_sweeps, uint64_t n_sweeps, uint64_t
     if (rc)
         return rc;
     std::vector<uint64_t> H;
-    rc = read_histogram(h, H);
+    rc = read_reduced_histogram(h, H);
     if (rc)
         return rc;
     // Sec. 3.3: ln g = ln H - ln W on visited energies, normalised to 2^N states.
@@ -1359,11 +1396,11 @@ int muca_save(muca_t h, const char *path)
     if (!fc.f)
         return fail(MUCA_EIO, "cannot open %s for writing", path);
     const int32_t L = h->L, layout = h->layout, wpb = h->wpb, order = h->order;
-    const int64_t nw = h->W;
+    const int64_t nw = h->W, first = h->walker0;
     const uint64_t seed = h->seed, t = h->t;
     const bool ok = put(fc.f, kCheckpointMagic, 8) && put(fc.f, &L, 1) && put(fc.f, &layout, 1) &&
                     put(fc.f, &nw, 1) && put(fc.f, &seed, 1) && put(fc.f, &wpb, 1) && put(fc.f, &order, 1) &&
-                    put(fc.f, &t, 1) && put(fc.f, h->lnW.data(), nb) && put(fc.f, H.data(), nb) &&
+                    put(fc.f, &t, 1) && put(fc.f, &first, 1) && put(fc.f, h->lnW.data(), nb) && put(fc.f, H.data(), nb) &&
                     put(fc.f, e.data(), W) && put(fc.f, bits.data(), bits.size());
     if (!ok || std::fflush(fc.f) != 0)
         return fail(MUCA_EIO, "writing %s failed", path);
@@ -1386,9 +1423,11 @@ int muca_load(const char *path, muca_t *out)
     if (!get(fc.f, magic, 8) || std::memcmp(magic, kCheckpointMagic, 8) != 0)
         return fail(MUCA_EIO, "%s is not a checkpoint of this library", path);
     if (!get(fc.f, &o.L, 1) || !get(fc.f, &o.layout, 1) || !get(fc.f, &o.n_walkers, 1) || !get(fc.f, &o.seed, 1) ||
-        !get(fc.f, &o.walkers_per_block, 1) || !get(fc.f, &order, 1) || !get(fc.f, &t, 1))
+        !get(fc.f, &o.walkers_per_block, 1) || !get(fc.f, &order, 1) || !get(fc.f, &t, 1) ||
+        !get(fc.f, &o.first_walker, 1))
         return fail(MUCA_EIO, "%s: truncated header", path);
     if (o.L < 4 || o.L > 64 || o.L % 4 != 0 || o.n_walkers < 1 || o.n_walkers > INT32_MAX ||
+        o.first_walker < 0 || o.first_walker > (int64_t)INT32_MAX - o.n_walkers ||
         (o.layout != MUCA_LAYOUT_INT8 && o.layout != MUCA_LAYOUT_PACKED))
         return fail(MUCA_EIO, "%s: invalid header", path);
     const size_t N = (size_t)o.L * o.L, W = (size_t)o.n_walkers, nb = N + 1, row = (N + 7) / 8;
@@ -1491,6 +1530,8 @@ int muca_batch_create(const muca_t *instances, int32_t n, muca_batch_t *out)
                         instances[i]->L);
         if (instances[i]->order != MUCA_ORDER_TYPEWRITER)
             return fail(MUCA_EINVAL, "instance %d: the batched kernel runs typewriter order only", i);
+        if (instances[i]->reducer)
+            return fail(MUCA_EINVAL, "instance %d has a histogram reducer: batches iterate instances alone", i);
         for (int32_t j = 0; j < i; ++j)
             if (instances[j] == instances[i])
                 return fail(MUCA_EINVAL, "instance %d appears twice", i);
@@ -2016,7 +2057,7 @@ int muca_production_jackknife(muca_t h, uint64_t therm_sweeps, int32_t n_chunks,
         rc = muca_sweep(h, sweeps_per_chunk, 1);
         if (rc)
             return rc;
-        rc = read_histogram(h, H);
+        rc = read_reduced_histogram(h, H);
         if (rc)
             return rc;
         for (size_t e = 0; e < B; ++e) {

@@ -500,7 +500,7 @@ __device__ __forceinline__ void sweep_block(const SweepArgs &a, int64_t wbase, i
     __syncthreads();
 
     if (active) {
-        const PhiloxKeys pk = make_keys(a.seed, (uint32_t)w);
+        const PhiloxKeys pk = make_keys(a.seed, a.walker0 + (uint32_t)w);
         const uint32_t tbase = (uint32_t)__cvta_generic_to_shared(sTab);
         uint32_t U[NW], C[NW], D[NW];
         uint32_t E = tbase + (uint32_t)e * (4u * kTableStride);

@@ -31,6 +31,7 @@ struct SweepArgs {
     unsigned long long *hist;   // [N+1], accumulated when recording
     uint32_t *err;              // device error word
     const uint32_t *skip = nullptr;   // when set and nonzero at launch: the launch does nothing
+    uint32_t walker0 = 0;             // global index of walker 0 (the Philox walker word is walker0 + w)
 };
 
 // Device state of an iteration whose recursion runs on the device (muca_iterate_device).
@@ -90,7 +91,7 @@ size_t random_smem_bytes(int L, int walkers_per_block, bool record);
 void set_full_kernel_enabled(bool on);
 
 // Draws the initial spins (tag 1 stream) and their energy indices.
-cudaError_t launch_init(int32_t L, int32_t layout, int64_t W, uint64_t seed, void *lattice,
+cudaError_t launch_init(int32_t L, int32_t layout, int64_t W, uint64_t seed, uint32_t walker0, void *lattice,
                         int32_t *energy, cudaStream_t s);
 
 // Packs lattices given as int8 in[walker][site] (+1/-1) and recomputes their energies.

@@ -76,7 +76,7 @@ __global__ void __launch_bounds__(1024) sweep_kernel(const SweepArgs a)
     uint32_t run_n = 0;
     if (active) {
         const uint32_t k0 = (uint32_t)a.seed, k1 = (uint32_t)(a.seed >> 32);
-        const uint32_t wid = (uint32_t)w;
+        const uint32_t wid = a.walker0 + (uint32_t)w;
         uint64_t t = a.t0;
         const uint64_t tend = a.t0 + a.n;
         while (t < tend) {
@@ -223,12 +223,12 @@ struct GivenRows {
 };
 
 template <typename RowT, int LAYOUT>
-__global__ void init_kernel(int32_t L, int64_t W, uint64_t seed, void *lattice, int32_t *energy)
+__global__ void init_kernel(int32_t L, int64_t W, uint64_t seed, uint32_t walker0, void *lattice, int32_t *energy)
 {
     const int64_t w = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (w >= W)
         return;
-    const InitRows<RowT> rows{L, (uint32_t)seed, (uint32_t)(seed >> 32), (uint32_t)w};
+    const InitRows<RowT> rows{L, (uint32_t)seed, (uint32_t)(seed >> 32), walker0 + (uint32_t)w};
     write_lattice<RowT, LAYOUT>(L, W, w, rows, lattice, energy);
 }
 
@@ -364,21 +364,22 @@ cudaError_t launch_sweep(const SweepArgs &a, int wpb, bool record, cudaStream_t 
 
 void set_full_kernel_enabled(bool on) { g_use_full_kernel = on; }
 
-cudaError_t launch_init(int32_t L, int32_t layout, int64_t W, uint64_t seed, void *lattice, int32_t *energy,
+cudaError_t launch_init(int32_t L, int32_t layout, int64_t W, uint64_t seed, uint32_t walker0, void *lattice,
+                        int32_t *energy,
                         cudaStream_t s)
 {
     const int threads = 128;
     const unsigned blocks = (unsigned)((W + threads - 1) / threads);
     if (L <= 32) {
         if (layout == MUCA_LAYOUT_PACKED)
-            init_kernel<uint32_t, MUCA_LAYOUT_PACKED><<<blocks, threads, 0, s>>>(L, W, seed, lattice, energy);
+            init_kernel<uint32_t, MUCA_LAYOUT_PACKED><<<blocks, threads, 0, s>>>(L, W, seed, walker0, lattice, energy);
         else
-            init_kernel<uint32_t, MUCA_LAYOUT_INT8><<<blocks, threads, 0, s>>>(L, W, seed, lattice, energy);
+            init_kernel<uint32_t, MUCA_LAYOUT_INT8><<<blocks, threads, 0, s>>>(L, W, seed, walker0, lattice, energy);
     } else {
         if (layout == MUCA_LAYOUT_PACKED)
-            init_kernel<unsigned long long, MUCA_LAYOUT_PACKED><<<blocks, threads, 0, s>>>(L, W, seed, lattice, energy);
+            init_kernel<unsigned long long, MUCA_LAYOUT_PACKED><<<blocks, threads, 0, s>>>(L, W, seed, walker0, lattice, energy);
         else
-            init_kernel<unsigned long long, MUCA_LAYOUT_INT8><<<blocks, threads, 0, s>>>(L, W, seed, lattice, energy);
+            init_kernel<unsigned long long, MUCA_LAYOUT_INT8><<<blocks, threads, 0, s>>>(L, W, seed, walker0, lattice, energy);
     }
     return cudaGetLastError();
 }

@@ -72,7 +72,7 @@ __global__ void __launch_bounds__(256) random_sweep_kernel(const SweepArgs a)
         }
     }
     const uint32_t k0 = (uint32_t)a.seed, k1 = (uint32_t)(a.seed >> 32);
-    const uint32_t wid = (uint32_t)w;
+    const uint32_t wid = a.walker0 + (uint32_t)w;
     const uint64_t tend = a.t0 + a.n;
     for (uint64_t tc = a.t0; tc < tend; tc += kSiteChunk) {
         const int m = tend - tc < (uint64_t)kSiteChunk ? (int)(tend - tc) : kSiteChunk;

@@ -87,8 +87,8 @@ def muca_create(L: int, n_walkers: int, seed: int) -> ctypes.c_void_p:
 
 
 def muca_create_ex(L: int, n_walkers: int, seed: int, layout: int = MUCA_LAYOUT_INT8,
-                   walkers_per_block: int = 0) -> ctypes.c_void_p:
-    o = muca_options(L, n_walkers, seed, layout, walkers_per_block)
+                   walkers_per_block: int = 0, first_walker: int = 0) -> ctypes.c_void_p:
+    o = muca_options(L, n_walkers, seed, layout, walkers_per_block, first_walker)
     h = ctypes.c_void_p()
     _check(C.load().muca_create_ex(ctypes.byref(o), ctypes.byref(h)))
     return h
@@ -117,6 +117,22 @@ def muca_measure_issue_rate(kind: int) -> float:
     v = ctypes.c_double()
     _check(C.load().muca_measure_issue_rate(kind, ctypes.byref(v)))
     return v.value
+
+
+def muca_set_histogram_reducer(h, fn, total_walkers: int = 0):
+    """fn(H) -> None receives the instance's histogram (a uint64 numpy view) and must
+    replace it in place by the sum over the simulation's instances; None removes it.
+    Returns the C callback object, which must stay alive while it is set."""
+    if fn is None:
+        _check(C.load().muca_set_histogram_reducer(h, None, None, 0))
+        return None
+
+    def tramp(ptr, n, ctx):
+        fn(np.ctypeslib.as_array(ptr, shape=(n,)))
+
+    cb = C.REDUCER(tramp)
+    _check(C.load().muca_set_histogram_reducer(h, ctypes.cast(cb, ctypes.c_void_p), None, total_walkers))
+    return cb
 
 
 def muca_set_site_order(h, order: int) -> None:
@@ -302,12 +318,13 @@ class Muca:
     """One multicanonical instance: n_walkers periodic L x L Ising lattices on the GPU."""
 
     def __init__(self, L: int, n_walkers: int, seed: int, layout: int = MUCA_LAYOUT_INT8,
-                 walkers_per_block: int = 0, stream=None, torch_allocator: bool = True):
+                 walkers_per_block: int = 0, stream=None, torch_allocator: bool = True, first_walker: int = 0):
         if torch_allocator:
             use_torch_allocator()
         self.L, self.N, self.W = L, L * L, n_walkers
         self.n_bins = self.N + 1
-        self._h = muca_create_ex(L, n_walkers, seed, layout, walkers_per_block)
+        self._reducer = None
+        self._h = muca_create_ex(L, n_walkers, seed, layout, walkers_per_block, first_walker)
         if n_walkers == MUCA_WALKERS_OPTIMAL:
             self.W = muca_get_info(self._h)[1]
         if stream is not None:
@@ -320,6 +337,7 @@ class Muca:
         if torch_allocator:
             use_torch_allocator()
         self = cls.__new__(cls)
+        self._reducer = None
         self._h = muca_load(path)
         L, W, _, _, _ = muca_get_info(self._h)
         self.L, self.N, self.W = L, L * L, W
@@ -327,6 +345,10 @@ class Muca:
         if stream is not None:
             muca_set_stream(self._h, int(getattr(stream, "cuda_stream", stream)))
         return self
+
+    def set_histogram_reducer(self, fn, total_walkers: int = 0) -> None:
+        """Sum histograms over the instances of one simulation (see muca.h)."""
+        self._reducer = muca_set_histogram_reducer(self._h, fn, total_walkers)
 
     def save(self, path: str) -> None:
         muca_save(self._h, path)

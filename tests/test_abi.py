@@ -70,7 +70,7 @@ def test_checkpoint_files_are_checked_without_gpu(lib, tmp_path):
     assert lib.muca_load(str(short).encode(), ctypes.byref(h)) == _lib.MUCA_EIO
     bad_l = tmp_path / "bad_l.muca"
     import struct
-    bad_l.write_bytes(b"MUCACKP1" + struct.pack("<iiqQiiQ", 6, 0, 10, 1, 0, 0, 0))
+    bad_l.write_bytes(b"MUCACKP1" + struct.pack("<iiqQiiQq", 6, 0, 10, 1, 0, 0, 0, 0))
     assert lib.muca_load(str(bad_l).encode(), ctypes.byref(h)) == _lib.MUCA_EIO
     assert lib.muca_load(None, ctypes.byref(h)) == _lib.MUCA_EINVAL
     assert not h.value
