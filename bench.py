@@ -773,6 +773,50 @@ def run_production_workload(args):
                    "stop_rule": "min/mean >= 0.8"}}))
 
 
+def run_traces_workload(args):
+    """Convergence traces of the weight iteration against the thermalization factor (the
+    protocol of Fig. A.1): L = 32, 26624 walkers, Eq. (7) schedule with f_therm in
+    {5, 10, 20, 30, 50}, stop at d_k < 1e-4; per iteration the Kullback-Leibler divergence
+    d_k (Eq. (6), the stop metric) and the Chebyshev distance d_c (Eq. (A.1)) of the
+    recorded histogram."""
+    import numpy as np
+    import torch
+    import __graft_entry__
+    __graft_entry__.build()
+    from paper_1707_00919_gb300 import muca as M
+    L, W = 32, 26624
+    N = L * L
+    acc = np.ones(N + 1, dtype=bool)
+    acc[[1, N - 1]] = False
+    stream = torch.cuda.Stream()
+    out = {}
+    for f in (5, 10, 20, 30, 50):
+        dk, dc = [], []
+
+        def observe(it, H, metric, n_therm, n_upd):
+            dk.append(metric)
+            m = H.sum() / (N - 1)
+            dc.append(float(np.max(np.abs(H[acc] / m - 1.0))) if m > 0 else float("inf"))
+        with M.Muca(L, W, SEED, stream=stream) as m:
+            m.set_iteration_observer(observe)
+            t0 = time.perf_counter()
+            st = m.iterate_until_flat(M.make_params(schedule=M.MUCA_SCHEDULE_PAPER, stop_rule=M.MUCA_STOP_KL,
+                                                    flat_threshold=1e-4, f_therm=float(f), max_iterations=3000))
+            torch.cuda.synchronize()
+            secs = time.perf_counter() - t0
+        out[f"f_therm_{f}"] = {"iterations": st.iterations, "converged": bool(st.converged), "seconds": secs,
+                               "attempts_per_walker": st.attempts_per_walker,
+                               "d_k": [float(f"{v:.4g}") for v in dk], "d_c": [float(f"{v:.4g}") for v in dc],
+                               "first_iteration_d_c_below_0.05":
+                                   next((i + 1 for i, v in enumerate(dc) if v < 0.05), None)}
+    print(json.dumps({
+        "metric": "convergence traces d_k and d_c per iteration against f_therm",
+        "value": out["f_therm_30"]["iterations"], "unit": "iterations", "higher_is_better": False, "n_gpus": 1,
+        "traces": out, "data": "synthetic: random +/-1 start, ln W = 0",
+        "config": {"workload": "convergence_traces_L32_W26624", "L": L, "walkers": W,
+                   "schedule": "Eq. (7)", "stop_rule": "d_k < 1e-4"}}))
+
+
 def run_convergence_workload(args):
     """Iterations and time until the weights converge against the walker count (the
     protocol of Figs. 3 and 4, Sec. 3.2): Eq. (7) schedule, stop when d_k < 1e-4
@@ -785,7 +829,11 @@ def run_convergence_workload(args):
     from paper_1707_00919_gb300 import muca as M
     dev = torch.cuda.current_device()
     stream = torch.cuda.Stream()
-    cases = {16: [1024, 2048, 4096, 8192, 16384, 32768], 32: [4096, 8192, 16384, 32768, 65536]}
+    # The first walker count of each size is the reference of the algorithmic speedup of
+    # Fig. 6 (the paper's is its 24-thread CPU run; W = 24 is affordable at L = 16 only:
+    # its update count starts large and grows by 1.1 per iteration once the range is
+    # covered; fewer seeds there, one warp runs the whole simulation)
+    cases = {16: [24, 1024, 2048, 4096, 8192, 16384, 32768], 32: [4096, 8192, 16384, 32768, 65536]}
     params = M.make_params(schedule=M.MUCA_SCHEDULE_PAPER, stop_rule=M.MUCA_STOP_KL, flat_threshold=1e-4,
                            max_iterations=3000)
     out = {}
@@ -794,7 +842,9 @@ def run_convergence_workload(args):
             rows = []
             for W in Ws:
                 its, secs, atts, conv = [], [], [], 0
-                for seed in range(1, args.seeds + 1):
+                per_walker = []
+                n_seeds = args.seeds if W > 24 else min(args.seeds, 8)
+                for seed in range(1, n_seeds + 1):
                     with M.Muca(L, W, seed, stream=stream) as m:
                         torch.cuda.synchronize()
                         t0 = time.perf_counter()
@@ -803,6 +853,7 @@ def run_convergence_workload(args):
                         secs.append(time.perf_counter() - t0)
                     its.append(st.iterations)
                     atts.append(st.attempts_per_walker * W)
+                    per_walker.append(st.attempts_per_walker)
                     conv += int(st.converged)
 
                 def stats(v):
@@ -810,7 +861,14 @@ def run_convergence_workload(args):
                     return {"mean": float(v.mean()), "err": float(v.std(ddof=1) / math.sqrt(len(v))) if len(v) > 1
                             else 0.0, "median": float(np.median(v))}
                 rows.append({"walkers": W, "iterations": stats(its), "seconds": stats(secs),
-                             "attempts": stats(atts), "converged": conv, "runs": args.seeds})
+                             "attempts": stats(atts), "attempts_per_walker": stats(per_walker),
+                             "converged": conv, "runs": n_seeds})
+            # Fig. 6: algorithmic speedup N_ref / N_W of the attempts per walker (medians)
+            ref = rows[0]
+            for r in rows:
+                r["algorithmic_speedup"] = ref["attempts_per_walker"]["median"] / r["attempts_per_walker"]["median"]
+                r["ideal_speedup"] = r["walkers"] / ref["walkers"]
+                r["speedup_reference_walkers"] = ref["walkers"]
             out[f"L{L}"] = rows
     l32 = {r["walkers"]: r for r in out["L32"]}
     print(json.dumps({
@@ -830,7 +888,8 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["native", "reference"], default="native")
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--workload", choices=["headline", "batch", "serve", "fliptime", "convergence", "production"],
+    ap.add_argument("--workload", choices=["headline", "batch", "serve", "fliptime", "convergence", "production",
+                                           "traces"],
                     default="headline")
     ap.add_argument("--seeds", type=int, default=32)
     ap.add_argument("--prod-seconds", type=float, default=10.0)
@@ -850,6 +909,9 @@ def main():
         return
     if args.workload == "production":
         run_production_workload(args)
+        return
+    if args.workload == "traces":
+        run_traces_workload(args)
         return
     if args.warmup < 3 and args.impl == "native":
         args.warmup = 3

@@ -236,6 +236,16 @@ int muca_set_weights(muca_t h, const double *lnW, size_t n_bins);
  * instance's own counts.  muca_iterate_device and muca_batch_create refuse instances
  * with a reducer (MUCA_EINVAL). */
 typedef void (*muca_histogram_reducer)(uint64_t *H, size_t n_bins, void *ctx);
+
+/* Observer of the weight iteration (for convergence traces such as the paper's Fig. A.1):
+ * fn(iteration, H, n_bins, metric, n_therm, n_updates, ctx) is called by
+ * muca_iterate_until_flat after the stop metric of every iteration (iteration counts
+ * from 1; H is the histogram the metric was computed from, valid during the call;
+ * n_therm and n_updates are the attempts per walker of that iteration).  fn == NULL
+ * removes it. */
+typedef void (*muca_iteration_observer)(int32_t iteration, const uint64_t *H, size_t n_bins, double metric,
+                                        uint64_t n_therm, uint64_t n_updates, void *ctx);
+int muca_set_iteration_observer(muca_t h, muca_iteration_observer fn, void *ctx);
 int muca_set_histogram_reducer(muca_t h, muca_histogram_reducer fn, void *ctx, int64_t total_walkers);
 
 /* Copies the current ln W into lnW_out[n_bins]. */

@@ -93,6 +93,9 @@ RELEASE_FN = ctypes.CFUNCTYPE(None, ctypes.c_void_p, ctypes.c_void_p)
 _P = ctypes.POINTER
 # muca_histogram_reducer: void (*)(uint64_t *H, size_t n_bins, void *ctx)
 REDUCER = ctypes.CFUNCTYPE(None, ctypes.POINTER(ctypes.c_uint64), ctypes.c_size_t, ctypes.c_void_p)
+# muca_iteration_observer: void (*)(int32_t, const uint64_t *, size_t, double, uint64_t, uint64_t, void *)
+OBSERVER = ctypes.CFUNCTYPE(None, ctypes.c_int32, ctypes.POINTER(ctypes.c_uint64), ctypes.c_size_t, ctypes.c_double,
+                            ctypes.c_uint64, ctypes.c_uint64, ctypes.c_void_p)
 _H = ctypes.c_void_p
 SIGNATURES = {
     "muca_default_params": (ctypes.c_int, [_P(muca_params)]),
@@ -101,6 +104,7 @@ SIGNATURES = {
     "muca_optimal_walkers": (ctypes.c_int, [ctypes.c_int32, ctypes.c_int32, _P(ctypes.c_int64), _P(ctypes.c_int32)]),
     "muca_iterate_device": (ctypes.c_int, [_H, _P(muca_params), ctypes.c_int32, _P(muca_stats)]),
     "muca_set_site_order": (ctypes.c_int, [_H, ctypes.c_int32]),
+    "muca_set_iteration_observer": (ctypes.c_int, [_H, ctypes.c_void_p, ctypes.c_void_p]),
     "muca_set_histogram_reducer": (ctypes.c_int, [_H, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int64]),
     "muca_measure_issue_rate": (ctypes.c_int, [ctypes.c_int32, _P(ctypes.c_double)]),
     "muca_set_lattice": (ctypes.c_int, [_H, _P(ctypes.c_int8), ctypes.c_size_t]),

@@ -120,6 +120,8 @@ struct muca_s {
     muca_histogram_reducer reducer = nullptr;   // sum over the instances of one simulation
     void *reducer_ctx = nullptr;
     int64_t total_walkers = 0;       // walkers of the whole simulation (Eq. (7)), 0 = W
+    muca_iteration_observer observer = nullptr;
+    void *observer_ctx = nullptr;
     int32_t kl_lo = -1, kl_hi = -1;  // range visited in the previous batched iteration
 };
 
@@ -923,6 +925,16 @@ int muca_set_histogram_reducer(muca_t h, muca_histogram_reducer fn, void *ctx, i
     return MUCA_OK;
 }
 
+int muca_set_iteration_observer(muca_t h, muca_iteration_observer fn, void *ctx)
+{
+    int rc = validate(h);
+    if (rc)
+        return rc;
+    h->observer = fn;
+    h->observer_ctx = fn ? ctx : nullptr;
+    return MUCA_OK;
+}
+
 int muca_set_site_order(muca_t h, int32_t order)
 {
     int rc = validate(h);
@@ -1104,6 +1116,8 @@ int muca_iterate_until_flat(muca_t h, const muca_params *p_in, muca_stats *stats
         else
             metric = chebyshev(N, H);
         flat = p.stop_rule == MUCA_STOP_MIN_MEAN ? metric >= p.flat_threshold : metric < p.flat_threshold;
+        if (h->observer)
+            h->observer(n, H.data(), H.size(), metric, n_therm, n_upd, h->observer_ctx);
         if (flat)
             break;
         // Eq. (4) in logarithms: ln W <- ln W - ln H on visited energies.

@@ -135,6 +135,22 @@ def muca_set_histogram_reducer(h, fn, total_walkers: int = 0):
     return cb
 
 
+def muca_set_iteration_observer(h, fn):
+    """fn(iteration, H, metric, n_therm, n_updates) is called after every iteration of
+    muca_iterate_until_flat (H: a uint64 copy); None removes it.  Returns the C callback
+    object, which must stay alive while it is set."""
+    if fn is None:
+        _check(C.load().muca_set_iteration_observer(h, None, None))
+        return None
+
+    def tramp(it, ptr, n, metric, n_therm, n_upd, ctx):
+        fn(it, np.ctypeslib.as_array(ptr, shape=(n,)).copy(), metric, n_therm, n_upd)
+
+    cb = C.OBSERVER(tramp)
+    _check(C.load().muca_set_iteration_observer(h, ctypes.cast(cb, ctypes.c_void_p), None))
+    return cb
+
+
 def muca_set_site_order(h, order: int) -> None:
     _check(C.load().muca_set_site_order(h, order))
 
@@ -345,6 +361,10 @@ class Muca:
         if stream is not None:
             muca_set_stream(self._h, int(getattr(stream, "cuda_stream", stream)))
         return self
+
+    def set_iteration_observer(self, fn) -> None:
+        """fn(iteration, H, metric, n_therm, n_updates) after every iteration."""
+        self._observer = muca_set_iteration_observer(self._h, fn)
 
     def set_histogram_reducer(self, fn, total_walkers: int = 0) -> None:
         """Sum histograms over the instances of one simulation (see muca.h)."""

@@ -93,3 +93,29 @@ def test_device_iteration_rejects_paper_schedule(muca_mod):
             m.iterate_device(M.make_params(schedule=M.MUCA_SCHEDULE_PAPER), 4, raise_on_fail=True)
         with pytest.raises(M.MucaError):
             m.iterate_device(M.make_params(), 0, raise_on_fail=True)
+
+
+def test_iteration_observer(muca_mod, orc):
+    """The observer sees every iteration once, in order, with the histogram the stop
+    metric came from (its total is walkers x recorded attempts) and that metric; the
+    oracle's metric history agrees."""
+    M = muca_mod
+    L, W, seed = 8, 128, 3
+    N = L * L
+    seen = []
+    p = M.make_params(schedule=M.MUCA_SCHEDULE_PAPER, stop_rule=M.MUCA_STOP_KL, flat_threshold=1e-3,
+                      max_iterations=400)
+    with M.Muca(L, W, seed) as m:
+        m.set_iteration_observer(lambda it, H, metric, nt, nu: seen.append((it, int(H.sum()), metric, nt, nu)))
+        st = m.iterate_until_flat(p)
+        m.set_iteration_observer(None)
+    assert [s[0] for s in seen] == list(range(1, st.iterations + 1))
+    assert all(total == W * nu for _, total, _, _, nu in seen)
+    assert seen[-1][2] == st.last_metric
+    assert sum(nt + nu for _, _, _, nt, nu in seen) == st.attempts_per_walker
+    s, e = orc.init(L, seed, W)
+    lnW = np.zeros(N + 1)
+    res, _, _, mh = orc.iterate(L, seed, s, e, lnW, 0,
+                                orc.make_params(schedule=1, stop_rule=1, flat_threshold=1e-3, max_iterations=400),
+                                history=True)
+    assert np.array_equal(np.array([x[2] for x in seen]), mh)
