@@ -334,6 +334,12 @@ int muca_get_info(muca_t h, int32_t *L, int64_t *n_walkers, uint64_t *attempt_co
  * invalid state. */
 int muca_synchronize(muca_t h);
 
+/* Waits at most `seconds` for the work queued so far on the instance's stream (polling,
+ * no blocking wait), then checks the device error word as muca_synchronize does.
+ * Returns MUCA_ETIMEOUT if the work is still running (it keeps running; a later call
+ * can wait again), MUCA_EINVAL for NULL or a negative limit. */
+int muca_synchronize_timeout(muca_t h, double seconds);
+
 /* Evaluates the library's device Philox4x32-10 on n counters (ctr[4*i .. 4*i+3]) with
  * one key (key[0] low, key[1] high 32 bits of the seed) into out[4*n].  Host buffers;
  * used to check the generator against independent implementations. */

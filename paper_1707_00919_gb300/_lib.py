@@ -104,6 +104,7 @@ SIGNATURES = {
     "muca_optimal_walkers": (ctypes.c_int, [ctypes.c_int32, ctypes.c_int32, _P(ctypes.c_int64), _P(ctypes.c_int32)]),
     "muca_iterate_device": (ctypes.c_int, [_H, _P(muca_params), ctypes.c_int32, _P(muca_stats)]),
     "muca_set_site_order": (ctypes.c_int, [_H, ctypes.c_int32]),
+    "muca_synchronize_timeout": (ctypes.c_int, [_H, ctypes.c_double]),
     "muca_set_iteration_observer": (ctypes.c_int, [_H, ctypes.c_void_p, ctypes.c_void_p]),
     "muca_set_histogram_reducer": (ctypes.c_int, [_H, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int64]),
     "muca_measure_issue_rate": (ctypes.c_int, [ctypes.c_int32, _P(ctypes.c_double)]),

@@ -13,6 +13,7 @@
 #include <mutex>
 #include <new>
 #include <string>
+#include <thread>
 #include <vector>
 
 #include <cuda_runtime.h>
@@ -1508,6 +1509,39 @@ int muca_synchronize(muca_t h)
     int rc = validate(h);
     if (rc)
         return rc;
+    return sync_and_check(h);
+}
+
+int muca_synchronize_timeout(muca_t h, double seconds)
+{
+    int rc = validate(h);
+    if (rc)
+        return rc;
+    if (!(seconds >= 0.0))
+        return fail(MUCA_EINVAL, "negative time limit");
+    cudaEvent_t ev = nullptr;
+    MUCA_CUDA(cudaEventCreateWithFlags(&ev, cudaEventDisableTiming), "event create");
+    cudaError_t err = cudaEventRecord(ev, h->stream);
+    const auto start = std::chrono::steady_clock::now();
+    bool done = false;
+    while (err == cudaSuccess) {
+        err = cudaEventQuery(ev);
+        if (err == cudaSuccess) {
+            done = true;
+            break;
+        }
+        if (err != cudaErrorNotReady)
+            break;
+        err = cudaSuccess;
+        if (std::chrono::duration<double>(std::chrono::steady_clock::now() - start).count() > seconds)
+            break;
+        std::this_thread::sleep_for(std::chrono::microseconds(50));
+    }
+    cudaEventDestroy(ev);
+    if (err != cudaSuccess)
+        return cuda_fail(err, "stream wait");
+    if (!done)
+        return fail(MUCA_ETIMEOUT, "the queued work did not finish within %.3f s", seconds);
     return sync_and_check(h);
 }
 

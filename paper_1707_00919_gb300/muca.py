@@ -151,6 +151,15 @@ def muca_set_iteration_observer(h, fn):
     return cb
 
 
+def muca_synchronize_timeout(h, seconds: float) -> bool:
+    """True when the queued work finished within the limit, False on MUCA_ETIMEOUT."""
+    rc = C.load().muca_synchronize_timeout(h, seconds)
+    if rc == C.MUCA_ETIMEOUT:
+        return False
+    _check(rc)
+    return True
+
+
 def muca_set_site_order(h, order: int) -> None:
     _check(C.load().muca_set_site_order(h, order))
 
@@ -362,6 +371,13 @@ class Muca:
             muca_set_stream(self._h, int(getattr(stream, "cuda_stream", stream)))
         return self
 
+    def synchronize(self, timeout: float | None = None) -> bool:
+        """Waits for the queued work (at most `timeout` seconds); False if it is still running."""
+        if timeout is None:
+            muca_synchronize(self._h)
+            return True
+        return muca_synchronize_timeout(self._h, timeout)
+
     def set_iteration_observer(self, fn) -> None:
         """fn(iteration, H, metric, n_therm, n_updates) after every iteration."""
         self._observer = muca_set_iteration_observer(self._h, fn)
@@ -458,9 +474,6 @@ class Muca:
     @property
     def attempt_counter(self) -> int:
         return muca_get_info(self._h)[2]
-
-    def synchronize(self) -> None:
-        muca_synchronize(self._h)
 
 
 # ---------------------------------------------------------------------------------

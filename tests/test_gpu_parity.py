@@ -306,3 +306,46 @@ def test_edge_walker_counts_and_empty_launches(muca_mod, orc, L, W, layout):
     Ho = orc.run(L, 31, s, eo, T, 2 * N, N + 7, True)
     assert t == 3 * N + 7
     assert np.array_equal(lat, s) and np.array_equal(e, eo) and np.array_equal(H, Ho)
+
+
+def test_bounded_wait(muca_mod):
+    """A wait with a time limit returns at the limit while long work is still running (it
+    is not interrupted) and reports completion once it is done."""
+    M = muca_mod
+    with M.Muca(64, 32768, 3) as m:
+        m.sweep(200, False)                     # about a second of work on one GPU
+        assert m.synchronize(timeout=0.0) is False
+        assert m.synchronize(timeout=60.0) is True
+        assert m.info()[2] == 200 * 64 * 64
+        with pytest.raises(M.MucaError):
+            M.muca_synchronize_timeout(m._h, -1.0)
+
+
+def test_orders_sample_the_same_distribution(muca_mod):
+    """Typewriter and random shared site order are both valid Metropolis chains for the
+    multicanonical weights (the shared sequence only correlates walkers, Sec. 2.3): with
+    the perfect weights of L = 8 both histograms are flat, and they agree within their
+    multinomial noise bin by bin."""
+    from conftest import load_exact_ln_dos
+    M = muca_mod
+    L = 8
+    N = L * L
+    lng = load_exact_ln_dos(L)
+    lnW = np.where(np.isfinite(lng), -lng, 0.0)
+    Hs = []
+    for order in (M.MUCA_ORDER_TYPEWRITER, M.MUCA_ORDER_RANDOM):
+        with M.Muca(L, 4096, 17 + order) as m:
+            m.site_order = order
+            m.set_weights(lnW)
+            m.sweep(200, False)
+            m.reset_histogram()
+            m.sweep(400, True)
+            Hs.append(m.get_histogram().astype(np.float64))
+    acc = np.isfinite(lng)
+    for H in Hs:
+        assert H[acc].min() / H[acc].mean() > 0.9
+    a, b = Hs[0][acc], Hs[1][acc]
+    # counts are autocorrelated (a walker needs many attempts to cross the range), so
+    # the bins differ by a few per cent, not by the multinomial 0.1 % (the oracle, which
+    # gives these histograms bit for bit, shows at most 3.5 %)
+    assert np.max(np.abs(a - b) / (0.5 * (a + b))) < 0.06
