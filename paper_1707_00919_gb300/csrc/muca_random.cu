@@ -20,7 +20,7 @@ template <typename RowT>
 size_t random_smem_bytes_t(int L, int wpb, bool record)
 {
     const size_t nb = (size_t)L * L + 1;
-    return align_up((nb * 5 + (record ? nb : 0)) * 4, 16) + (size_t)kSiteChunk * 16 + (size_t)L * wpb * sizeof(RowT);
+    return align_up((nb * 5 + (record ? nb : 0)) * 4, 16) + (size_t)(kSiteChunk + 1) * 16 + (size_t)L * wpb * sizeof(RowT);
 }
 
 template <typename RowT, int LAYOUT, bool RECORD>
@@ -38,7 +38,7 @@ __global__ void __launch_bounds__(256) random_sweep_kernel(const SweepArgs a)
     // per site of the chunk: row offsets (row * wpb) of the rows above, at and below,
     // and x | x_left << 8 | x_right << 16; shared by all walkers of the block
     uint4 *sSite = reinterpret_cast<uint4 *>(smem + align_up((size_t)(nb * 5 + (RECORD ? nb : 0)) * 4, 16));
-    RowT *sRows = reinterpret_cast<RowT *>(reinterpret_cast<unsigned char *>(sSite) + (size_t)kSiteChunk * 16);
+    RowT *sRows = reinterpret_cast<RowT *>(reinterpret_cast<unsigned char *>(sSite) + (size_t)(kSiteChunk + 1) * 16);
     const int tid = threadIdx.x;
     const int64_t w = (int64_t)blockIdx.x * wpb + tid;
     bool active = w < a.W;
@@ -90,6 +90,8 @@ __global__ void __launch_bounds__(256) random_sweep_kernel(const SweepArgs a)
             sSite[j] = make_uint4((uint32_t)(yu * wpb), (uint32_t)(y * wpb), (uint32_t)(yd * wpb),
                                   (uint32_t)(x | (xl << 8) | (xr << 16)));
         }
+        if (tid == 0)   // look-ahead record past the chunk's last site: any valid rows
+            sSite[m] = make_uint4(0u, 0u, 0u, 0u);
         __syncthreads();
         if (!active)
             continue;
@@ -110,26 +112,18 @@ __global__ void __launch_bounds__(256) random_sweep_kernel(const SweepArgs a)
                 C ^= (site.y == prow) ? pbit : (RowT)0;
                 D ^= (site.z == prow) ? pbit : (RowT)0;
             }
-            uint4 nsite = site;
-            RowT nU = 0, nC = 0, nD = 0;
-            if (j + 1 < m) {
-                nsite = sSite[j + 1];
-                nU = col[nsite.x];
-                nC = col[nsite.y];
-                nD = col[nsite.z];
-            }
+            const uint4 nsite = sSite[j + 1];   // j + 1 <= m: the spare record at the end
+            const RowT nU = col[nsite.x], nC = col[nsite.y], nD = col[nsite.z];
             const int x = (int)(site.w & 0xFFu), xl = (int)((site.w >> 8) & 0xFFu), xr = (int)(site.w >> 16);
             const uint32_t sx = bit_at(C, x);
             const uint32_t k = (sx ^ bit_at(U, x)) + (sx ^ bit_at(D, x)) + (sx ^ bit_at(C, xl)) + (sx ^ bit_at(C, xr));
             const uint32_t thr = sT[e * 5 + (int)k];
             const bool acc = r < thr || thr == 0xFFFFFFFFu;
             const RowT bx = (RowT)1 << x;
-            if (acc) {
-                col[site.y] = C ^ bx;
-                e += 2 - (int)k;
-            }
+            col[site.y] = C ^ (acc ? bx : (RowT)0);   // unconditional: the row is unchanged on a rejection
+            e += acc ? 2 - (int)k : 0;
             if (RECORD)
-                atomicAdd(&sH[e], 1u);
+                asm volatile("red.shared.add.u32 [%0], 1;" ::"r"((uint32_t)__cvta_generic_to_shared(sH + e)));
             pacc = acc;
             prow = site.y;
             pbit = bx;
