@@ -376,6 +376,7 @@ def run_native(args):
     rec_attempts = WALKERS * SWEEPS_PER_ITER * N
     achieved_tops = OPS_PER_ATTEMPT * rec_attempts / rec_launch_s / 1e12
     traffic = profiled_traffic()
+    lattice_bytes = 2 * WALKERS * N   # int8 lattices read and written once per launch
     # measured issue rates of the instruction classes the sweep uses (context for the peak)
     probe = {name: M.muca_measure_issue_rate(kind) / 1e12
              for name, kind in (("xor3_alu", M.MUCA_PROBE_XOR), ("imad", M.MUCA_PROBE_MAD),
@@ -412,7 +413,13 @@ def run_native(args):
                      "ops_per_attempt": OPS_PER_ATTEMPT,
                      "peak_basis": f"{sm_count} SMs x 4 issue slots x 32 lanes x {sm_max_mhz:.0f} MHz",
                      "measured_issue_tops": {k: round(v, 3) for k, v in probe.items()},
-                     "measured_philox_words_per_s": philox_words},
+                     "measured_philox_words_per_s": philox_words,
+                     # lattice traffic of the same launch against HBM (not the bound)
+                     "hbm": {"algorithmic_bytes": lattice_bytes, "algorithmic_gbs": lattice_bytes / rec_launch_s / 1e9,
+                             "dram_gbs": (traffic / rec_launch_s / 1e9) if traffic else None,
+                             "peak_gbs": peaks.get("hbm_gbs"),
+                             "frac": (lattice_bytes / rec_launch_s / 1e9 / peaks["hbm_gbs"])
+                             if peaks.get("hbm_gbs") else None}},
         "clocks": clocks.summary(),
     }
     m.close()
