@@ -445,7 +445,7 @@ def run_native(args):
     result["random_site_order"] = {"attempts_per_s": rnd_rate, "ns_per_flip": 1e9 / rnd_rate,
                                    "protocol": "perfect weights, 3 sweeps to equilibrate, median of 5 launches "
                                                "of 2 recorded sweeps in random shared site order"}
-    if rank == 0 and not args.no_cpu_baseline:
+    if rank == 0 and ws == 1 and not args.no_cpu_baseline:   # the oracle baseline at N = 1 only
         rate, cores, wall = cpu_baseline(lnW, WALKERS)
         result["cpu_baseline"] = {"value": rate, "unit": "attempts/s", "cores": cores, "kind": "oracle",
                                   "sample": f"one step ({THERM_SWEEPS}+{SWEEPS_PER_ITER} sweeps) of all "
