@@ -70,3 +70,31 @@ def test_sharded_walkers_match_single_process(tmp_path, orc):
     for r in range(2):
         assert np.array_equal(np.load(tmp_path / f"H_{r}.npy"), np.array(ref_hist))
         assert np.array_equal(np.load(tmp_path / f"lnW_{r}.npy"), lnW)
+
+
+def _bench_rank_main(rank, world, port, out_dir):
+    """The benchmark's multi-rank plumbing (rank discovery from the environment, gloo
+    group, barrier, max over ranks) as torchrun would drive it."""
+    import sys
+    sys.path.insert(0, os.path.dirname(os.path.dirname(os.path.abspath(__file__))))
+    os.environ.update({"WORLD_SIZE": str(world), "RANK": str(rank), "LOCAL_RANK": str(rank),
+                       "MASTER_ADDR": "127.0.0.1", "MASTER_PORT": str(port)})
+    import bench
+    ws, r, local = bench.dist_env()
+    dist = bench.init_dist(ws)
+    bench.barrier(dist)
+    value = bench.max_over_ranks(dist, 1.5 + r)
+    with open(os.path.join(out_dir, f"max_{rank}.txt"), "w") as f:
+        f.write(f"{ws} {r} {local} {value}")
+    dist.destroy_process_group()
+
+
+def test_bench_plumbing_two_ranks(tmp_path):
+    pytest.importorskip("torch")
+    import torch.multiprocessing as tmp
+    port = _free_port()
+    tmp.spawn(_bench_rank_main, args=(2, port, str(tmp_path)), nprocs=2, join=True)
+    for r in range(2):
+        ws, rank, local, value = (tmp_path / f"max_{r}.txt").read_text().split()
+        assert (int(ws), int(rank), int(local)) == (2, r, r)
+        assert float(value) == 2.5           # every rank sees the slowest rank's time
