@@ -564,6 +564,8 @@ __device__ __forceinline__ void sweep_block(const SweepArgs &a, int64_t wbase, i
             }
         }
         e = (int32_t)((E - tbase) / (4u * kTableStride));
+        if (E < tbase || e > N || (E - tbase) % (4u * kTableStride) != 0u)   // corrupted energy address
+            atomicOr(a.err, kErrEnergyRange);
     }
     __syncthreads();
     if (RECORD)
