@@ -51,7 +51,8 @@ def config_dict():
     return {"workload": WORKLOAD, "L": L_SIDE, "walkers": WALKERS, "layout": "int8 [site][walker]",
             "therm_sweeps": THERM_SWEEPS, "sweeps_per_iter": SWEEPS_PER_ITER, "energy_bins": L_SIDE**2 + 1,
             "stop_rule": "min/mean >= 0.8", "max_iterations": MAX_ITERATIONS,
-            "l2": "flushed between timed steps (256 MiB write)", "parallelism": "independent instance per GPU"}
+            "l2": "flushed between timed steps (256 MiB write)", "parallelism": "independent instance per GPU",
+            "arithmetic": "u32 thresholds, random words and counts; int8 spins; u64 histogram; f64 weights"}
 
 
 def exact_ln_dos(L: int):
@@ -393,7 +394,7 @@ def run_native(args):
         "higher_is_better": True,
         "scaling": "weak",
         "vs_baseline": None,
-        "dtype": "int32/u32 (spins int8, histogram u64, weights f64 on host)",
+        "dtype": "u32",
         "data": "synthetic: random +/-1 Ising lattices from the seed",
         "config": config_dict(),
         "time_to_flat_s": ttf,
@@ -479,7 +480,7 @@ def run_reference(args):
         "metric": "spin-flip attempts/s (and time-to-flat H) at L=32, 16384 walkers; % of integer-issue roofline",
         "value": value, "unit": "attempts/s", "n_gpus": ws, "steps": args.steps, "warmup": args.warmup,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
-        "dtype": "int32/u32 (spins int8, histogram u64, weights f64)", "data": "synthetic",
+        "dtype": "u32", "data": "synthetic",
         "config": config_dict(),
         "cpu_baseline": {"value": value, "unit": "attempts/s", "cores": cores_used, "kind": "oracle",
                          "sample": f"{sample_walkers} walkers x ({THERM_SWEEPS}+{SWEEPS_PER_ITER}) sweeps per step"},
