@@ -65,47 +65,79 @@ def lib():
     global _lib
     with _lock:
         if _lib is None:
-            path = build()
-            L = ctypes.CDLL(path)
-            P = ctypes.POINTER
-            u32, u64, i32, i64, dbl, i8 = (ctypes.c_uint32, ctypes.c_uint64, ctypes.c_int32,
-                                           ctypes.c_int64, ctypes.c_double, ctypes.c_int8)
-            sig = {
-                "orc_philox4x32_10": (None, [P(u32), P(u32), P(u32)]),
-                "orc_random_word": (u32, [u64, u32, u32, u64]),
-                "orc_energy_index": (i32, [i32, P(i8)]),
-                "orc_init": (None, [i32, u64, u32, i64, P(i8), P(i32)]),
-                "orc_build_table": (None, [i32, P(dbl), P(u32)]),
-                "orc_accept": (ctypes.c_int, [u32, u32]),
-                "orc_run": (None, [i32, u64, u32, i64, P(i8), P(i32), P(u32), u64, u64, i32, P(u64)]),
-                "orc_run_random": (None, [i32, u64, u32, i64, P(i8), P(i32), P(u32), u64, u64, i32, P(u64)]),
-                "orc_random_site": (i32, [i32, u64, u64]),
-                "orc_update_weights": (None, [i32, P(dbl), P(u64)]),
-                "orc_accessible": (ctypes.c_int, [i32, i32]),
-                "orc_min_over_mean": (dbl, [i32, P(u64)]),
-                "orc_width": (i32, [i32, P(u64)]),
-                "orc_accessible_in_range": (i32, [i32, P(u64)]),
-                "orc_kl_support": (i32, [i32, i32, i32, P(u64)]),
-                "orc_kullback_leibler": (dbl, [i32, P(u64), dbl]),
-                "orc_exp": (dbl, [dbl]),
-                "orc_log": (dbl, [dbl]),
-                "orc_chebyshev": (dbl, [i32, P(u64)]),
-                "orc_iterate": (i32, [i32, i64, u64, P(i8), P(i32), P(dbl), P(u64), P(Params),
-                                      P(dbl), P(dbl), P(Result)]),
-                "orc_ln_dos": (None, [i32, P(dbl), P(u64), P(dbl)]),
-                "orc_production": (i32, [i32, i64, u64, P(i8), P(i32), P(dbl), P(u64), u64, u64,
-                                         P(u64), P(dbl), i32]),
-                "orc_dos_bruteforce": (i32, [i32, P(u64)]),
-                "orc_jackknife": (i32, [i32, P(dbl), P(u64), i32, P(dbl), P(dbl)]),
-                "orc_canonical": (None, [i32, P(dbl), dbl, P(dbl), P(dbl)]),
-                "orc_dos_transfer": (i32, [i32, P(u64), P(u64)]),
-            }
-            for name, (res, args) in sig.items():
-                f = getattr(L, name)
-                f.restype = res
-                f.argtypes = args
-            _lib = L
+            _lib = _bind(build())
     return _lib
+
+
+def build_variant(sources: list[str], path: str) -> str:
+    """Compiles other oracle sources (e.g. a copy with a planted mistake, for the tests
+    that check the pins catch it) into `path` with the same options."""
+    cmd = ["gcc", "-std=c11", "-O2", "-fPIC", "-shared", "-ffp-contract=off", "-fno-fast-math", "-o", path] + \
+        list(sources) + ["-lm"]
+    subprocess.run(cmd, check=True)
+    return path
+
+
+class using:
+    """Context manager: the binding's functions call the library at `path` inside it."""
+
+    def __init__(self, path: str):
+        self.path = path
+
+    def __enter__(self):
+        global _lib
+        with _lock:
+            self.saved = _lib
+            _lib = _bind(self.path)
+        return self
+
+    def __exit__(self, *exc):
+        global _lib
+        with _lock:
+            _lib = self.saved
+
+
+def _bind(path: str):
+    """Loads a compiled oracle library and declares its C signatures."""
+    L = ctypes.CDLL(path)
+    P = ctypes.POINTER
+    u32, u64, i32, i64, dbl, i8 = (ctypes.c_uint32, ctypes.c_uint64, ctypes.c_int32,
+                                   ctypes.c_int64, ctypes.c_double, ctypes.c_int8)
+    sig = {
+        "orc_philox4x32_10": (None, [P(u32), P(u32), P(u32)]),
+        "orc_random_word": (u32, [u64, u32, u32, u64]),
+        "orc_energy_index": (i32, [i32, P(i8)]),
+        "orc_init": (None, [i32, u64, u32, i64, P(i8), P(i32)]),
+        "orc_build_table": (None, [i32, P(dbl), P(u32)]),
+        "orc_accept": (ctypes.c_int, [u32, u32]),
+        "orc_run": (None, [i32, u64, u32, i64, P(i8), P(i32), P(u32), u64, u64, i32, P(u64)]),
+        "orc_run_random": (None, [i32, u64, u32, i64, P(i8), P(i32), P(u32), u64, u64, i32, P(u64)]),
+        "orc_random_site": (i32, [i32, u64, u64]),
+        "orc_update_weights": (None, [i32, P(dbl), P(u64)]),
+        "orc_accessible": (ctypes.c_int, [i32, i32]),
+        "orc_min_over_mean": (dbl, [i32, P(u64)]),
+        "orc_width": (i32, [i32, P(u64)]),
+        "orc_accessible_in_range": (i32, [i32, P(u64)]),
+        "orc_kl_support": (i32, [i32, i32, i32, P(u64)]),
+        "orc_kullback_leibler": (dbl, [i32, P(u64), dbl]),
+        "orc_exp": (dbl, [dbl]),
+        "orc_log": (dbl, [dbl]),
+        "orc_chebyshev": (dbl, [i32, P(u64)]),
+        "orc_iterate": (i32, [i32, i64, u64, P(i8), P(i32), P(dbl), P(u64), P(Params),
+                              P(dbl), P(dbl), P(Result)]),
+        "orc_ln_dos": (None, [i32, P(dbl), P(u64), P(dbl)]),
+        "orc_production": (i32, [i32, i64, u64, P(i8), P(i32), P(dbl), P(u64), u64, u64,
+                                 P(u64), P(dbl), i32]),
+        "orc_dos_bruteforce": (i32, [i32, P(u64)]),
+        "orc_jackknife": (i32, [i32, P(dbl), P(u64), i32, P(dbl), P(dbl)]),
+        "orc_canonical": (None, [i32, P(dbl), dbl, P(dbl), P(dbl)]),
+        "orc_dos_transfer": (i32, [i32, P(u64), P(u64)]),
+    }
+    for name, (res, args) in sig.items():
+        f = getattr(L, name)
+        f.restype = res
+        f.argtypes = args
+    return L
 
 
 def _ptr(a: np.ndarray, ctype):
