@@ -123,7 +123,18 @@ typedef struct {
     double growth;               /* PAPER: after full coverage N <- floor(growth N) + 1    */
     int32_t max_iterations;      /* stop with MUCA_ENOTCONVERGED after this many           */
     double deadline_s;           /* > 0: stop with MUCA_ETIMEOUT after this wall time      */
+    int32_t resume;              /* 1: continue the iteration state the instance keeps (see
+                                    below), 0: start afresh (w' = 0, no range visited)    */
 } muca_params;
+
+/* Iteration state kept by an instance between calls of muca_iterate_until_flat, updated
+ * after every weight update and stored by muca_save: the width w' and the range
+ * [lo, hi] of the energies visited in the previous iteration (the w of Sec. 3 and the
+ * Kullback-Leibler reference width of Eq. (6)), whether the whole range had been covered
+ * (Eq. (7) then gives way to the growth rule) and the previous N_updates.  With
+ * params.resume = 1 a run stopped by max_iterations or the deadline, or restored from a
+ * checkpoint, continues the schedule as one uninterrupted call would have.  The batched
+ * and served iterations and muca_iterate_device start afresh (they reject resume = 1). */
 
 /* Statistics of a weight iteration. */
 typedef struct {
@@ -168,12 +179,13 @@ int muca_destroy(muca_t h);
  * n = n_walkers * N) and recomputes the energies on the device.
  * muca_set_attempt_counter: sets t, the counter of the next attempt.
  * muca_save: writes the state and the creation options to a binary file (little-endian:
- * 8-byte magic "MUCACKP1", L, layout, n_walkers, seed, walkers_per_block, site order, t,
- * first_walker,
+ * 8-byte magic "MUCACKP2", L, layout, n_walkers, seed, walkers_per_block, site order, t,
+ * first_walker, the iteration state (int32 w', lo, hi, covered; uint64 previous N_updates),
  * ln W[N+1] FP64, H[N+1] uint64, energies int32[n_walkers], then per walker N bits,
  * rounded up to whole bytes, bit i of byte i/8 set for a down spin at site i).
  * muca_load: creates an instance from such a file (same options) and restores the state;
- * the stored energies must equal those recomputed from the stored lattices.
+ * the stored energies must equal those recomputed from the stored lattices.  Files of the
+ * earlier format "MUCACKP1" (no iteration state) load with a fresh iteration state.
  * Errors: MUCA_EINVAL (NULL, wrong n, a spin other than +1 / -1), MUCA_EIO (file
  * cannot be opened, written or read; not a checkpoint; inconsistent content),
  * MUCA_ENOMEM, MUCA_ECUDA. */

@@ -52,7 +52,7 @@ class muca_params(ctypes.Structure):
                 ("flat_threshold", ctypes.c_double), ("therm_sweeps", ctypes.c_uint64),
                 ("sweeps_per_iter", ctypes.c_uint64), ("f_therm", ctypes.c_double),
                 ("z", ctypes.c_double), ("factor", ctypes.c_double), ("growth", ctypes.c_double),
-                ("max_iterations", ctypes.c_int32), ("deadline_s", ctypes.c_double)]
+                ("max_iterations", ctypes.c_int32), ("deadline_s", ctypes.c_double), ("resume", ctypes.c_int32)]
 
 
 class muca_stats(ctypes.Structure):

@@ -91,6 +91,14 @@ uint64_t max_recorded_attempts(int wpb) { return 0xFFFFFFFFull / (uint64_t)std::
 
 }  // namespace
 
+// State of the weight iteration carried from one iteration to the next (Sec. 3):
+// extent and range of the energies visited in the previous iteration, whether the whole
+// range had been covered, and the previous N_updates.
+struct IterSchedule {
+    int32_t prev_width = 0, prev_lo = -1, prev_hi = -1, full = 0;
+    uint64_t upd_prev = 0;
+};
+
 struct muca_s {
     int32_t L = 0, N = 0;
     int64_t W = 0;
@@ -124,12 +132,14 @@ struct muca_s {
     muca_iteration_observer observer = nullptr;
     void *observer_ctx = nullptr;
     int32_t kl_lo = -1, kl_hi = -1;  // range visited in the previous batched iteration
+    IterSchedule sched;              // iteration state kept between calls (params.resume)
 };
 
 namespace {
 
 // Checkpoint files (muca_save / muca_load).
-const char kCheckpointMagic[8] = {'M', 'U', 'C', 'A', 'C', 'K', 'P', '1'};
+const char kCheckpointMagic[8] = {'M', 'U', 'C', 'A', 'C', 'K', 'P', '2'};
+const char kCheckpointMagicV1[8] = {'M', 'U', 'C', 'A', 'C', 'K', 'P', '1'};   // no iteration state
 
 struct FileCloser {
     FILE *f;
@@ -585,6 +595,8 @@ int check_iteration_params(const muca_params &p, muca_t h)
         return fail(MUCA_EINVAL, "batched iteration supports the fixed-sweep schedule");
     if (p.stop_rule < MUCA_STOP_MIN_MEAN || p.stop_rule > MUCA_STOP_CHEBYSHEV || p.max_iterations < 1)
         return fail(MUCA_EINVAL, "bad stop rule or max_iterations");
+    if (p.resume)
+        return fail(MUCA_EINVAL, "batched iterations start afresh (resume = 0)");
     if (p.sweeps_per_iter * (uint64_t)h->N > 0xFFFFFFFFull / 256ull)
         return fail(MUCA_EINVAL, "sweeps_per_iter too large for one recording launch");
     if (h->t % (uint64_t)h->N != 0)
@@ -1065,12 +1077,15 @@ int muca_iterate_until_flat(muca_t h, const muca_params *p_in, muca_stats *stats
         return fail(MUCA_EINVAL, "unknown stop rule %d", p.stop_rule);
     if (p.max_iterations < 1)
         return fail(MUCA_EINVAL, "max_iterations must be positive");
+    if (p.resume != 0 && p.resume != 1)
+        return fail(MUCA_EINVAL, "resume must be 0 or 1");
     const auto start = std::chrono::steady_clock::now();
     const int32_t N = h->N;
     std::vector<uint64_t> H;
-    int32_t prev_width = 0, prev_lo = -1, prev_hi = -1;
-    bool full = false;
-    uint64_t upd_prev = 0, spent = 0;
+    const IterSchedule s0 = p.resume ? h->sched : IterSchedule{};
+    int32_t prev_width = s0.prev_width, prev_lo = s0.prev_lo, prev_hi = s0.prev_hi;
+    bool full = s0.full != 0;
+    uint64_t upd_prev = s0.upd_prev, spent = 0;
     int32_t n = 0;
     bool flat = false, timed_out = false;
     double metric = 0.0;
@@ -1135,6 +1150,11 @@ int muca_iterate_until_flat(muca_t h, const muca_params *p_in, muca_stats *stats
             prev_lo = prev_hi = -1;
         }
         upd_prev = n_upd;
+        h->sched.prev_width = prev_width;
+        h->sched.prev_lo = prev_lo;
+        h->sched.prev_hi = prev_hi;
+        h->sched.full = full ? 1 : 0;
+        h->sched.upd_prev = upd_prev;
         if (p.deadline_s > 0.0) {
             const double el = std::chrono::duration<double>(std::chrono::steady_clock::now() - start).count();
             if (el > p.deadline_s) {
@@ -1198,6 +1218,8 @@ int muca_iterate_device(muca_t h, const muca_params *p_in, int32_t iterations_pe
         muca_default_params(&p);
     if (p.schedule != MUCA_SCHEDULE_SWEEPS)
         return fail(MUCA_EINVAL, "muca_iterate_device runs the fixed-sweep schedule only");
+    if (p.resume)
+        return fail(MUCA_EINVAL, "muca_iterate_device starts the iteration afresh (resume = 0)");
     if (h->reducer)
         return fail(MUCA_EINVAL, "muca_iterate_device cannot reduce histograms over instances");
     if (p.stop_rule < MUCA_STOP_MIN_MEAN || p.stop_rule > MUCA_STOP_CHEBYSHEV)
@@ -1413,9 +1435,11 @@ int muca_save(muca_t h, const char *path)
     const int32_t L = h->L, layout = h->layout, wpb = h->wpb, order = h->order;
     const int64_t nw = h->W, first = h->walker0;
     const uint64_t seed = h->seed, t = h->t;
+    const int32_t sched[4] = {h->sched.prev_width, h->sched.prev_lo, h->sched.prev_hi, h->sched.full};
     const bool ok = put(fc.f, kCheckpointMagic, 8) && put(fc.f, &L, 1) && put(fc.f, &layout, 1) &&
                     put(fc.f, &nw, 1) && put(fc.f, &seed, 1) && put(fc.f, &wpb, 1) && put(fc.f, &order, 1) &&
-                    put(fc.f, &t, 1) && put(fc.f, &first, 1) && put(fc.f, h->lnW.data(), nb) && put(fc.f, H.data(), nb) &&
+                    put(fc.f, &t, 1) && put(fc.f, &first, 1) && put(fc.f, sched, 4) &&
+                    put(fc.f, &h->sched.upd_prev, 1) && put(fc.f, h->lnW.data(), nb) && put(fc.f, H.data(), nb) &&
                     put(fc.f, e.data(), W) && put(fc.f, bits.data(), bits.size());
     if (!ok || std::fflush(fc.f) != 0)
         return fail(MUCA_EIO, "writing %s failed", path);
@@ -1435,16 +1459,33 @@ int muca_load(const char *path, muca_t *out)
     std::memset(&o, 0, sizeof o);
     int32_t order = 0;
     uint64_t t = 0;
-    if (!get(fc.f, magic, 8) || std::memcmp(magic, kCheckpointMagic, 8) != 0)
+    if (!get(fc.f, magic, 8) ||
+        (std::memcmp(magic, kCheckpointMagic, 8) != 0 && std::memcmp(magic, kCheckpointMagicV1, 8) != 0))
         return fail(MUCA_EIO, "%s is not a checkpoint of this library", path);
+    const bool has_sched = std::memcmp(magic, kCheckpointMagic, 8) == 0;
+    IterSchedule sched;
+    int32_t sched_words[4] = {0, -1, -1, 0};
     if (!get(fc.f, &o.L, 1) || !get(fc.f, &o.layout, 1) || !get(fc.f, &o.n_walkers, 1) || !get(fc.f, &o.seed, 1) ||
         !get(fc.f, &o.walkers_per_block, 1) || !get(fc.f, &order, 1) || !get(fc.f, &t, 1) ||
-        !get(fc.f, &o.first_walker, 1))
+        !get(fc.f, &o.first_walker, 1) ||
+        (has_sched && (!get(fc.f, sched_words, 4) || !get(fc.f, &sched.upd_prev, 1))))
         return fail(MUCA_EIO, "%s: truncated header", path);
+    sched.prev_width = sched_words[0];
+    sched.prev_lo = sched_words[1];
+    sched.prev_hi = sched_words[2];
+    sched.full = sched_words[3];
     if (o.L < 4 || o.L > 64 || o.L % 4 != 0 || o.n_walkers < 1 || o.n_walkers > INT32_MAX ||
         o.first_walker < 0 || o.first_walker > (int64_t)INT32_MAX - o.n_walkers ||
         (o.layout != MUCA_LAYOUT_INT8 && o.layout != MUCA_LAYOUT_PACKED))
         return fail(MUCA_EIO, "%s: invalid header", path);
+    {
+        const int32_t nbins = o.L * o.L + 1;
+        const bool no_range = sched.prev_lo == -1 && sched.prev_hi == -1 && sched.prev_width == 0;
+        const bool range_ok = sched.prev_lo >= 0 && sched.prev_lo <= sched.prev_hi && sched.prev_hi < nbins &&
+                              sched.prev_width == sched.prev_hi - sched.prev_lo + 1;
+        if ((!no_range && !range_ok) || (sched.full != 0 && sched.full != 1))
+            return fail(MUCA_EIO, "%s: invalid iteration state", path);
+    }
     const size_t N = (size_t)o.L * o.L, W = (size_t)o.n_walkers, nb = N + 1, row = (N + 7) / 8;
     std::vector<double> lnW(nb);
     std::vector<uint64_t> H(nb);
@@ -1481,6 +1522,7 @@ int muca_load(const char *path, muca_t *out)
     if (err != cudaSuccess)
         return cleanup(cuda_fail(err, "histogram upload"));
     h->t = t;
+    h->sched = sched;
     *out = h;
     return MUCA_OK;
 }
@@ -1921,7 +1963,7 @@ int muca_server_submit(muca_server_t s, const muca_request *r, int64_t *id)
         return fail(MUCA_EINVAL, "n_walkers out of range");
     if (r->layout == MUCA_LAYOUT_AUTO || r->walkers_per_block == MUCA_WPB_TUNE)
         return fail(MUCA_EINVAL, "requests take an explicit layout and block size (0 = default)");
-    if (r->params.schedule != MUCA_SCHEDULE_SWEEPS || r->params.max_iterations < 1 ||
+    if (r->params.schedule != MUCA_SCHEDULE_SWEEPS || r->params.max_iterations < 1 || r->params.resume ||
         r->params.stop_rule < MUCA_STOP_MIN_MEAN || r->params.stop_rule > MUCA_STOP_CHEBYSHEV ||
         r->params.sweeps_per_iter * (uint64_t)r->L * (uint64_t)r->L > 0xFFFFFFFFull / 256ull)
         return fail(MUCA_EINVAL, "request parameters: fixed-sweep schedule, valid stop rule and sweeps");

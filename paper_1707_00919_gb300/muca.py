@@ -334,9 +334,9 @@ class IterationStats:
 def make_params(schedule: int = MUCA_SCHEDULE_SWEEPS, stop_rule: int = MUCA_STOP_MIN_MEAN,
                 flat_threshold: float = 0.8, therm_sweeps: int = 31, sweeps_per_iter: int = 100,
                 f_therm: float = 30.0, z: float = 2.25, factor: float = 6.0, growth: float = 1.1,
-                max_iterations: int = 1000, deadline_s: float = 0.0) -> muca_params:
+                max_iterations: int = 1000, deadline_s: float = 0.0, resume: bool = False) -> muca_params:
     return muca_params(schedule, stop_rule, flat_threshold, therm_sweeps, sweeps_per_iter, f_therm, z,
-                       factor, growth, max_iterations, deadline_s)
+                       factor, growth, max_iterations, deadline_s, 1 if resume else 0)
 
 
 class Muca:

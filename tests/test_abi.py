@@ -72,6 +72,15 @@ def test_checkpoint_files_are_checked_without_gpu(lib, tmp_path):
     import struct
     bad_l.write_bytes(b"MUCACKP1" + struct.pack("<iiqQiiQq", 6, 0, 10, 1, 0, 0, 0, 0))
     assert lib.muca_load(str(bad_l).encode(), ctypes.byref(h)) == _lib.MUCA_EIO
+    # the current format carries the iteration state after first_walker
+    head = b"MUCACKP2" + struct.pack("<iiqQiiQq", 8, 0, 2, 1, 32, 0, 0, 0)
+    for state, ok in [((0, -1, -1, 0), True), ((65, 0, 64, 1), True), ((3, 5, 4, 0), False),
+                      ((2, 64, 65, 0), False), ((4, 1, 2, 0), False), ((3, 0, 2, 2), False)]:
+        f = tmp_path / "v2.muca"
+        f.write_bytes(head + struct.pack("<iiiiQ", *state, 7) + bytes(16))   # body cut short
+        rc = lib.muca_load(str(f).encode(), ctypes.byref(h))
+        assert rc == _lib.MUCA_EIO, state
+        assert ("truncated" in lib.muca_last_error().decode()) == ok, state
     assert lib.muca_load(None, ctypes.byref(h)) == _lib.MUCA_EINVAL
     assert not h.value
 

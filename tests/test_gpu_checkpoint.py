@@ -89,3 +89,57 @@ def test_bad_lattice_rejected(muca_mod):
             m.set_lattice(bad)
         with pytest.raises(M.MucaError):
             m.set_lattice(np.ones((4, 63), dtype=np.int8))
+
+
+@pytest.mark.parametrize("schedule", ["paper", "sweeps"])
+def test_iteration_resumes_across_calls_and_checkpoints(muca_mod, tmp_path, schedule):
+    """A weight iteration cut by max_iterations continues, with params.resume, as one
+    uninterrupted call: the same N_therm / N_updates sequence of Sec. 3, the same
+    Kullback-Leibler reference width, the same weights bit for bit, in the same instance
+    or in one restored from a checkpoint.  Without resume the schedule starts afresh."""
+    M = muca_mod
+    L, W, seed = 8, 128, 4
+    if schedule == "paper":
+        kw = dict(schedule=M.MUCA_SCHEDULE_PAPER, stop_rule=M.MUCA_STOP_KL, flat_threshold=1e-4)
+    else:
+        kw = dict(stop_rule=M.MUCA_STOP_KL, flat_threshold=0.01, therm_sweeps=31, sweeps_per_iter=100)
+    p_all = M.make_params(max_iterations=3000, **kw)
+
+    def run(m, p, log):
+        m.set_iteration_observer(lambda it, H, metric, nt, nu: log.append((nt, nu, metric)))
+        st = m.iterate_until_flat(p)
+        m.set_iteration_observer(None)
+        return st
+
+    whole = []
+    with M.Muca(L, W, seed) as m:
+        st = run(m, p_all, whole)
+        ref = (m.get_weights(), m.info()[2])
+    assert st.converged and st.iterations >= 4
+    k = st.iterations // 2
+    p_cut = M.make_params(max_iterations=k, **kw)
+    p_resume = M.make_params(max_iterations=3000, resume=True, **kw)
+    path = str(tmp_path / "cut.muca")
+    for restore in (False, True):
+        log = []
+        with M.Muca(L, W, seed) as m:
+            first = run(m, p_cut, log)
+            assert not first.converged and first.iterations == k
+            m.save(path)
+            if restore:
+                with M.Muca.load(path) as r:
+                    second = run(r, p_resume, log)
+                    got = (r.get_weights(), r.info()[2])
+            else:
+                second = run(m, p_resume, log)
+                got = (m.get_weights(), m.info()[2])
+        assert second.converged and k + second.iterations == st.iterations
+        assert log == whole
+        assert np.array_equal(got[0], ref[0]) and got[1] == ref[1]
+    fresh = []
+    with M.Muca.load(path) as r:
+        run(r, M.make_params(max_iterations=1, **kw), fresh)
+    if schedule == "paper":
+        assert fresh[0][:2] != whole[k][:2]      # N_therm, N_updates of w = 10 again
+    else:
+        assert fresh[0][:2] == whole[k][:2]      # fixed sweeps; only the KL reference differs

@@ -113,3 +113,49 @@ def test_noalloc_rejects_sizes_beyond_its_limits(env):
         r.t0 = 5
         with pytest.raises(M.MucaError):
             M.muca_batch_sweep_noalloc([r], 1, False)
+
+
+def test_noalloc_flags_an_energy_off_the_grid(env):
+    """A walker whose stored energy index lies outside 0..L*L sets the error word's
+    energy bit and is left untouched (no table read, lattice and energy kept); the
+    instance's other walkers and the other instances sweep exactly as before."""
+    torch, M, C = env
+    specs = [(16, 64, 0, 5, -1), (32, 100, 1, 99, 32 * 32 + 1), (24, 100, 0, 97, 10 ** 6), (8, 33, 0, None, 0)]
+    inst, raws, bufs, before = [], [], [], []
+    for i, (L, W, lay, bad, val) in enumerate(specs):
+        m = M.Muca(L, W, 800 + i, layout=lay)
+        m.set_weights(weights(L, 10 + i))
+        r, b = raw_copy(torch, C, m, L, W, lay, 800 + i)
+        if bad is not None:
+            b["energy"][bad] = val
+        before.append((b["lattice"].cpu().numpy().copy(), b["energy"].cpu().numpy().copy()))
+        inst.append(m)
+        raws.append(r)
+        bufs.append(b)
+    torch.cuda.synchronize()
+    with M.Batch(inst) as batch:
+        for m in inst:
+            m.reset_histogram()
+        batch.sweep(2, True)
+        M.muca_batch_sweep_noalloc(raws, 2, True)
+        torch.cuda.synchronize()
+        for (L, W, lay, bad, val), m, b, (lat0, en0) in zip(specs, inst, bufs, before):
+            buf = b["lattice"].cpu().numpy()
+            view = (lambda x: x.view(np.uint32 if L <= 32 else np.uint64)) if lay == 1 else (lambda x: x)
+            got, ref = from_layout(view(buf), L, lay, W), m.get_lattice()
+            en = b["energy"].cpu().numpy()
+            err = int(b["err"].item())
+            keep = np.ones(W, bool)
+            if bad is None:
+                assert err == 0
+                assert np.array_equal(b["hist"].cpu().numpy().view(np.uint64), m.get_histogram())
+            else:
+                assert err == 1, (L, err)
+                keep[bad] = False
+                assert np.array_equal(got[bad], from_layout(view(lat0), L, lay, W)[bad])
+                assert en[bad] == en0[bad] == val
+                assert not np.array_equal(got[keep], from_layout(view(lat0), L, lay, W)[keep])
+            assert np.array_equal(got[keep], ref[keep]), (L, W, lay)
+            assert np.array_equal(en[keep], m.get_energies()[keep]), (L, W, lay)
+    for m in inst:
+        m.close()
