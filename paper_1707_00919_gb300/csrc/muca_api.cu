@@ -1365,8 +1365,10 @@ int muca_get_lattice(muca_t h, int8_t *out, size_t n)
     cudaError_t err = muca::launch_unpack(h->L, h->layout, h->W, h->d_lattice, tmp, h->stream);
     if (err == cudaSuccess)
         err = cudaMemcpyAsync(out, tmp, total, cudaMemcpyDeviceToHost, h->stream);
+    // the buffer goes back to the allocator only after every use of it has finished
+    const cudaError_t sync = cudaStreamSynchronize(h->stream);
     if (err == cudaSuccess)
-        err = cudaStreamSynchronize(h->stream);
+        err = sync;
     device_free(h->alloc, tmp);
     if (err != cudaSuccess)
         return cuda_fail(err, "lattice read");
@@ -1390,8 +1392,9 @@ int muca_set_lattice(muca_t h, const int8_t *spins, size_t n)
     cudaError_t err = cudaMemcpyAsync(tmp, spins, total, cudaMemcpyHostToDevice, h->stream);
     if (err == cudaSuccess)
         err = muca::launch_pack(h->L, h->layout, h->W, tmp, h->d_lattice, h->d_energy, h->stream);
+    const cudaError_t sync = cudaStreamSynchronize(h->stream);
     if (err == cudaSuccess)
-        err = cudaStreamSynchronize(h->stream);
+        err = sync;
     device_free(h->alloc, tmp);
     if (err != cudaSuccess)
         return cuda_fail(err, "lattice upload");
