@@ -455,7 +455,8 @@ __device__ __forceinline__ void sweep_block(const SweepArgs &a, int64_t wbase, i
     const int nthr = blockDim.x;
     uint32_t *sTab = reinterpret_cast<uint32_t *>(smem);
     const int tid = threadIdx.x;
-    const SmemRows<L> rows{smem + align_up((size_t)NB * kTableStride * 4, 16), wpb, tid};
+    constexpr int NR = NB + 2 * kTableGuard;   // table rows: energies -2 .. N + 2
+    const SmemRows<L> rows{smem + align_up((size_t)NR * kTableStride * 4, 16), wpb, tid};
     const int lane = tid & 31;
     const bool in_item = tid < wpb;
     const int64_t w = wbase + tid;
@@ -463,9 +464,10 @@ __device__ __forceinline__ void sweep_block(const SweepArgs &a, int64_t wbase, i
     bool active = in_item && w < a.W;
     const bool warp_full = in_item && (w0 + 32 <= a.W) && (a.W % 16 == 0);
 
-    for (int i = tid; i < NB * kTableStride; i += nthr) {
-        const int e = i / kTableStride, k = i - e * kTableStride;
-        sTab[i] = k < 5 ? a.table[e * 5 + k] : 0u;
+    for (int i = tid; i < NR * kTableStride; i += nthr) {
+        const int r = i / kTableStride, k = i - r * kTableStride;
+        const int e = r - kTableGuard;
+        sTab[i] = (k < 5 && e >= 0 && e <= N) ? a.table[e * 5 + k] : 0u;
     }
 
     if (LAYOUT == MUCA_LAYOUT_PACKED) {
@@ -501,7 +503,7 @@ __device__ __forceinline__ void sweep_block(const SweepArgs &a, int64_t wbase, i
 
     if (active) {
         const PhiloxKeys pk = make_keys(a.seed, a.walker0 + (uint32_t)w);
-        const uint32_t tbase = (uint32_t)__cvta_generic_to_shared(sTab);
+        const uint32_t tbase = (uint32_t)__cvta_generic_to_shared(sTab) + kTableGuard * kTableStride * 4u;
         uint32_t U[NW], C[NW], D[NW];
         uint32_t E = tbase + (uint32_t)e * (4u * kTableStride);
         if (!PARTIAL) {
@@ -570,7 +572,7 @@ __device__ __forceinline__ void sweep_block(const SweepArgs &a, int64_t wbase, i
     __syncthreads();
     if (RECORD)
         for (int i = tid; i < NB; i += nthr) {
-            const uint32_t v = sTab[i * kTableStride + kHistSlot];
+            const uint32_t v = sTab[(i + kTableGuard) * kTableStride + kHistSlot];
             if (v)
                 atomicAdd(&a.hist[i], (unsigned long long)v);
         }

@@ -13,6 +13,10 @@ namespace muca {
 // energy, thresholds in words 0..4, the block's histogram count in word kHistSlot.
 constexpr int kTableStride = 7;
 constexpr int kHistSlot = 5;
+// Zero rows below energy 0 and above N: the threshold candidates loaded ahead of a
+// decision lie within two rows of the current energy, so they stay inside the table
+// even for energies that do not match the lattice.
+constexpr int kTableGuard = 2;
 
 // Device error word bits.
 constexpr uint32_t kErrEnergyRange = 1u;   // a walker's energy index was off the grid

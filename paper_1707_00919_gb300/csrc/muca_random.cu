@@ -15,12 +15,38 @@ namespace muca {
 namespace {
 
 constexpr int kSiteChunk = 1024;   // attempts whose sites are drawn at once
+constexpr int kSpare = 4;          // records past a chunk's end, read by the look-ahead
+constexpr uint32_t kCleanBit = 1u << 31;   // in the first record of a clean group (offset word)
+constexpr int kRandStride = 6;     // words per table row: thresholds of k = 0..4, histogram count
+constexpr int kRandGuard = 2;      // zero rows below energy 0 and above N (speculative loads)
 
 template <typename RowT>
-size_t random_smem_bytes_t(int L, int wpb, bool record)
+size_t random_smem_bytes_t(int L, int wpb, bool)
 {
-    const size_t nb = (size_t)L * L + 1;
-    return align_up((nb * 5 + (record ? nb : 0)) * 4, 16) + (size_t)(kSiteChunk + 1) * 16 + (size_t)L * wpb * sizeof(RowT);
+    const size_t rows = (size_t)L * L + 1 + 2 * kRandGuard;
+    return align_up(rows * kRandStride * 4, 16) + (size_t)(kSiteChunk + kSpare) * 16 + (size_t)L * wpb * sizeof(RowT);
+}
+
+// Spin s (0 / 1) of the site and its number k of antiparallel neighbours, from the rows
+// above, at and below it; w holds x, x - 1 and x + 1 (mod L) in its low three bytes.
+template <typename RowT>
+__device__ __forceinline__ void site_count(RowT U, RowT C, RowT D, uint32_t w, uint32_t &s, uint32_t &k)
+{
+    const int x = (int)(w & 0xFFu), xl = (int)((w >> 8) & 0xFFu), xr = (int)((w >> 16) & 0xFFu);
+    s = bit_at(C, x);
+    k = (s ^ bit_at(U, x)) + (s ^ bit_at(D, x)) + (s ^ bit_at(C, xl)) + (s ^ bit_at(C, xr));
+}
+
+__device__ __forceinline__ uint32_t lds_word(uint32_t addr)
+{
+    uint32_t v;
+    asm volatile("ld.shared.u32 %0, [%1];" : "=r"(v) : "r"(addr));
+    return v;
+}
+
+__device__ __forceinline__ void hist_count(uint32_t E)
+{
+    asm volatile("red.shared.add.u32 [%0+20], 1;" ::"r"(E));
 }
 
 template <typename RowT, int LAYOUT, bool RECORD>
@@ -31,24 +57,26 @@ __global__ void __launch_bounds__(256) random_sweep_kernel(const SweepArgs a)
         return;
     const int L = a.L;
     const int N = L * L;
-    const int nb = N + 1;
+    const int nrows = N + 1 + 2 * kRandGuard;
     const int wpb = blockDim.x;
+    // table row r holds energy r - kRandGuard; the guard rows are zero (never accepted)
     uint32_t *sT = reinterpret_cast<uint32_t *>(smem);
-    uint32_t *sH = sT + nb * 5;
-    // per site of the chunk: row offsets (row * wpb) of the rows above, at and below,
-    // and x | x_left << 8 | x_right << 16; shared by all walkers of the block
-    uint4 *sSite = reinterpret_cast<uint4 *>(smem + align_up((size_t)(nb * 5 + (RECORD ? nb : 0)) * 4, 16));
-    RowT *sRows = reinterpret_cast<RowT *>(reinterpret_cast<unsigned char *>(sSite) + (size_t)(kSiteChunk + 1) * 16);
+    // per site of the chunk: byte offsets of the rows above (plus kCleanBit, see below),
+    // at and below it in a walker's column, and x | x_left << 8 | x_right << 16 | y << 24;
+    // shared by all walkers of the block
+    uint4 *sSite = reinterpret_cast<uint4 *>(smem + align_up((size_t)nrows * kRandStride * 4, 16));
+    RowT *sRows = reinterpret_cast<RowT *>(reinterpret_cast<unsigned char *>(sSite) + (size_t)(kSiteChunk + kSpare) * 16);
     const int tid = threadIdx.x;
     const int64_t w = (int64_t)blockIdx.x * wpb + tid;
     bool active = w < a.W;
 
-    for (int i = tid; i < nb * 5; i += wpb)
-        sT[i] = a.table[i];
-    if (RECORD)
-        for (int i = tid; i < nb; i += wpb)
-            sH[i] = 0u;
+    for (int i = tid; i < nrows * kRandStride; i += wpb) {
+        const int r = i / kRandStride, k = i - r * kRandStride;
+        const int e = r - kRandGuard;
+        sT[i] = (k < 5 && e >= 0 && e <= N) ? a.table[e * 5 + k] : 0u;
+    }
     RowT *col = sRows + tid;   // this walker's rows: col[y * wpb]
+    unsigned char *cbytes = reinterpret_cast<unsigned char *>(col);
     int32_t e = 0;
     if (active) {
         if (LAYOUT == MUCA_LAYOUT_PACKED) {
@@ -71,9 +99,14 @@ __global__ void __launch_bounds__(256) random_sweep_kernel(const SweepArgs a)
             active = false;
         }
     }
+    constexpr uint32_t kRowBytes = 4u * kRandStride;
+    const uint32_t tbase = (uint32_t)__cvta_generic_to_shared(sT) + kRandGuard * kRowBytes;
+    uint32_t E = tbase + (uint32_t)e * kRowBytes;   // byte address of the current energy's row
+    auto row = [&](uint32_t off) { return *reinterpret_cast<const RowT *>(cbytes + off); };
     const uint32_t k0 = (uint32_t)a.seed, k1 = (uint32_t)(a.seed >> 32);
     const uint32_t wid = a.walker0 + (uint32_t)w;
     const uint64_t tend = a.t0 + a.n;
+    const uint32_t rb = (uint32_t)wpb * (uint32_t)sizeof(RowT);   // bytes between rows of a column
     for (uint64_t tc = a.t0; tc < tend; tc += kSiteChunk) {
         const int m = tend - tc < (uint64_t)kSiteChunk ? (int)(tend - tc) : kSiteChunk;
         __syncthreads();   // the previous chunk's sites are consumed (and the setup done)
@@ -87,73 +120,140 @@ __global__ void __launch_bounds__(256) random_sweep_kernel(const SweepArgs a)
             const int y = (int)(i / (uint32_t)L), x = (int)i - y * L;
             const int yu = (y == 0) ? L - 1 : y - 1, yd = (y == L - 1) ? 0 : y + 1;
             const int xl = (x == 0) ? L - 1 : x - 1, xr = (x == L - 1) ? 0 : x + 1;
-            sSite[j] = make_uint4((uint32_t)(yu * wpb), (uint32_t)(y * wpb), (uint32_t)(yd * wpb),
-                                  (uint32_t)(x | (xl << 8) | (xr << 16)));
+            sSite[j] = make_uint4((uint32_t)yu * rb, (uint32_t)y * rb, (uint32_t)yd * rb,
+                                  (uint32_t)(x | (xl << 8) | (xr << 16) | (y << 24)));
         }
-        if (tid == 0)   // look-ahead record past the chunk's last site: any valid rows
-            sSite[m] = make_uint4(0u, 0u, 0u, 0u);
+        if (tid < kSpare)   // look-ahead records past the chunk's last site: any valid rows
+            sSite[m + tid] = make_uint4(0u, 0u, 0u, 0u);
+        __syncthreads();
+        // Groups of four attempts that share a Philox block start at t = 0 mod 4.  A group
+        // is clean when none of its sites coincides with or neighbours an earlier site
+        // of the group or of the previous group of the chunk: then the neighbour counts
+        // read before the previous group's flips are those at its decisions.
+        const int j0 = (int)((4u - (uint32_t)(tc & 3)) & 3u);
+        const int ngroups = m > j0 ? (m - j0) / 4 : 0;
+        for (int gi = tid; gi < ngroups; gi += wpb) {
+            const int jb = j0 + 4 * gi;
+            const int first = gi > 0 ? jb - 4 : jb;
+            bool clean = true;
+            for (int a1 = jb; a1 < jb + 4; ++a1) {
+                const uint32_t wa = sSite[a1].w;
+                const int xa = (int)(wa & 0xFFu), ya = (int)((wa >> 24) & 0x3Fu);
+                for (int b1 = first; b1 < a1; ++b1) {
+                    const uint32_t wb = sSite[b1].w;
+                    int dx = xa - (int)(wb & 0xFFu), dy = ya - (int)((wb >> 24) & 0x3Fu);
+                    dx = dx < 0 ? dx + L : dx;
+                    dy = dy < 0 ? dy + L : dy;
+                    const bool near = (dx == 0 && (dy == 0 || dy == 1 || dy == L - 1)) ||
+                                      (dy == 0 && (dx == 1 || dx == L - 1));
+                    clean = clean && !near;
+                }
+            }
+            if (clean)
+                sSite[jb].x |= kCleanBit;
+        }
         __syncthreads();
         if (!active)
             continue;
-        // The rows of the next attempt's site are loaded before the current attempt
-        // decides (its flip is then applied to them where the rows coincide), which
-        // takes the row loads off the attempt-to-attempt chain (energy, threshold
-        // load, compare).
-        uint4 site = sSite[0];
-        RowT U = col[site.x], C = col[site.y], D = col[site.z];
-        bool pacc = false;
-        uint32_t prow = 0xFFFFFFFFu;   // row offset of the previous attempt's site
-        RowT pbit = 0;
+        auto flip = [&](uint32_t off, uint32_t w, bool acc) {
+            atomicXor(reinterpret_cast<RowT *>(cbytes + off), acc ? (RowT)1 << (w & 0xFFu) : (RowT)0);
+        };
+        // one attempt on rows read after every earlier flip
+        auto single = [&](int jj, uint32_t r) {
+            const uint4 rc = sSite[jj];
+            uint32_t sx, k;
+            site_count(row(rc.x & ~kCleanBit), row(rc.y), row(rc.z), rc.w, sx, k);
+            const bool acc = r < lds_word(E + 4u * k);
+            flip(rc.y, rc.w, acc);
+            E = acc ? E + (2u - k) * kRowBytes : E;
+            if (RECORD)
+                hist_count(E);
+        };
+        auto words = [&](uint64_t tt) {
+            const uint64_t blk = tt >> 2;
+            const uint4 q = philox4x32_10(make_uint4((uint32_t)blk, (uint32_t)(blk >> 32), wid, kTagMetropolis), k0, k1);
+            // clamped so that "r < T" also accepts every attempt when T = 0xFFFFFFFF
+            return make_uint4(min(q.x, 0xFFFFFFFEu), min(q.y, 0xFFFFFFFEu), min(q.z, 0xFFFFFFFEu),
+                              min(q.w, 0xFFFFFFFEu));
+        };
+        auto word_at = [](const uint4 &q, uint32_t u) { return u == 0 ? q.x : u == 1 ? q.y : u == 2 ? q.z : q.w; };
         int j = 0;
         uint64_t t = tc;
-        auto attempt = [&](uint32_t r) {
-            if (pacc) {   // the previous attempt flipped a site after these rows were read
-                U ^= (site.x == prow) ? pbit : (RowT)0;
-                C ^= (site.y == prow) ? pbit : (RowT)0;
-                D ^= (site.z == prow) ? pbit : (RowT)0;
+        for (; j < m && (t & 3) != 0; ++j, ++t)   // the head of a launch that starts inside a Philox block
+            single(j, word_at(words(t), (uint32_t)(t & 3)));
+        if (m - j >= 4) {
+            uint4 c0 = sSite[j], c1 = sSite[j + 1], c2 = sSite[j + 2], c3 = sSite[j + 3];
+            uint32_t kc0, kc1, kc2, kc3, sx;
+            site_count(row(c0.x & ~kCleanBit), row(c0.y), row(c0.z), c0.w, sx, kc0);
+            site_count(row(c1.x & ~kCleanBit), row(c1.y), row(c1.z), c1.w, sx, kc1);
+            site_count(row(c2.x & ~kCleanBit), row(c2.y), row(c2.z), c2.w, sx, kc2);
+            site_count(row(c3.x & ~kCleanBit), row(c3.y), row(c3.z), c3.w, sx, kc3);
+            for (; m - j >= 4; j += 4, t += 4) {
+                // the next group's sites and rows, read before this group's flips
+                const uint4 n0 = sSite[j + 4], n1 = sSite[j + 5], n2 = sSite[j + 6], n3 = sSite[j + 7];
+                const RowT u0 = row(n0.x & ~kCleanBit), m0 = row(n0.y), d0r = row(n0.z);
+                const RowT u1 = row(n1.x & ~kCleanBit), m1 = row(n1.y), d1r = row(n1.z);
+                const RowT u2 = row(n2.x & ~kCleanBit), m2 = row(n2.y), d2r = row(n2.z);
+                const RowT u3 = row(n3.x & ~kCleanBit), m3 = row(n3.y), d3r = row(n3.z);
+                const uint4 q = words(t);
+                if (c0.x & kCleanBit) {
+                    // Each decision takes one of two thresholds loaded one attempt
+                    // ahead (the previous attempt rejected / flipped); the counts are
+                    // known for the whole group.
+                    const uint32_t s0 = (2u - kc0) * kRowBytes, s1 = (2u - kc1) * kRowBytes,
+                                   s2 = (2u - kc2) * kRowBytes, s3 = (2u - kc3) * kRowBytes;
+                    const uint32_t T00 = lds_word(E + 4u * kc0);
+                    const uint32_t T10 = lds_word(E + 4u * kc1), T11 = lds_word(E + s0 + 4u * kc1);
+                    const bool a0 = q.x < T00;
+                    flip(c0.y, c0.w, a0);
+                    const uint32_t E1 = a0 ? E + s0 : E;
+                    if (RECORD)
+                        hist_count(E1);
+                    const uint32_t T20 = lds_word(E1 + 4u * kc2), T21 = lds_word(E1 + s1 + 4u * kc2);
+                    const bool a1 = q.y < (a0 ? T11 : T10);
+                    flip(c1.y, c1.w, a1);
+                    const uint32_t E2 = a1 ? E1 + s1 : E1;
+                    if (RECORD)
+                        hist_count(E2);
+                    const uint32_t T30 = lds_word(E2 + 4u * kc3), T31 = lds_word(E2 + s2 + 4u * kc3);
+                    const bool a2 = q.z < (a1 ? T21 : T20);
+                    flip(c2.y, c2.w, a2);
+                    const uint32_t E3 = a2 ? E2 + s2 : E2;
+                    if (RECORD)
+                        hist_count(E3);
+                    const bool a3 = q.w < (a2 ? T31 : T30);
+                    flip(c3.y, c3.w, a3);
+                    E = a3 ? E3 + s3 : E3;
+                    if (RECORD)
+                        hist_count(E);
+                } else {
+                    single(j, q.x);
+                    single(j + 1, q.y);
+                    single(j + 2, q.z);
+                    single(j + 3, q.w);
+                }
+                site_count(u0, m0, d0r, n0.w, sx, kc0);
+                site_count(u1, m1, d1r, n1.w, sx, kc1);
+                site_count(u2, m2, d2r, n2.w, sx, kc2);
+                site_count(u3, m3, d3r, n3.w, sx, kc3);
+                c0 = n0;
+                c1 = n1;
+                c2 = n2;
+                c3 = n3;
             }
-            const uint4 nsite = sSite[j + 1];   // j + 1 <= m: the spare record at the end
-            const RowT nU = col[nsite.x], nC = col[nsite.y], nD = col[nsite.z];
-            const int x = (int)(site.w & 0xFFu), xl = (int)((site.w >> 8) & 0xFFu), xr = (int)(site.w >> 16);
-            const uint32_t sx = bit_at(C, x);
-            const uint32_t k = (sx ^ bit_at(U, x)) + (sx ^ bit_at(D, x)) + (sx ^ bit_at(C, xl)) + (sx ^ bit_at(C, xr));
-            const uint32_t thr = sT[e * 5 + (int)k];
-            const bool acc = r < thr || thr == 0xFFFFFFFFu;
-            const RowT bx = (RowT)1 << x;
-            col[site.y] = C ^ (acc ? bx : (RowT)0);   // unconditional: the row is unchanged on a rejection
-            e += acc ? 2 - (int)k : 0;
-            if (RECORD)
-                asm volatile("red.shared.add.u32 [%0], 1;" ::"r"((uint32_t)__cvta_generic_to_shared(sH + e)));
-            pacc = acc;
-            prow = site.y;
-            pbit = bx;
-            site = nsite;
-            U = nU;
-            C = nC;
-            D = nD;
-            ++j;
-            ++t;
-        };
-        while (j < m) {
-            // one Philox call serves the attempts of its block (t & 3 = 0 .. 3)
-            const uint64_t blk = t >> 2;
-            const uint4 rw = philox4x32_10(make_uint4((uint32_t)blk, (uint32_t)(blk >> 32), wid, kTagMetropolis),
-                                           k0, k1);
-            const int u0 = (int)(t & 3);
-            if (u0 <= 0 && j < m)
-                attempt(rw.x);
-            if (u0 <= 1 && j < m)
-                attempt(rw.y);
-            if (u0 <= 2 && j < m)
-                attempt(rw.z);
-            if (j < m)
-                attempt(rw.w);
         }
+        for (; j < m; ++j, ++t)   // the tail of a launch that ends inside a Philox block
+            single(j, word_at(words(t), (uint32_t)(t & 3)));
+    }
+    if (active) {
+        e = (int32_t)((E - tbase) / kRowBytes);
+        if (E < tbase || e > N || (E - tbase) % kRowBytes != 0u)   // corrupted energy address
+            atomicOr(a.err, kErrEnergyRange);
     }
     __syncthreads();
     if (RECORD)
-        for (int i = tid; i < nb; i += wpb) {
-            const uint32_t v = sH[i];
+        for (int i = tid; i <= N; i += wpb) {
+            const uint32_t v = sT[(i + kRandGuard) * kRandStride + 5];
             if (v)
                 atomicAdd(&a.hist[i], (unsigned long long)v);
         }

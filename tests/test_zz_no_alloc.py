@@ -159,3 +159,37 @@ def test_noalloc_flags_an_energy_off_the_grid(env):
             assert np.array_equal(en[keep], m.get_energies()[keep]), (L, W, lay)
     for m in inst:
         m.close()
+
+
+def test_noalloc_energies_that_do_not_match_the_lattices(env, orc):
+    """Caller-owned energies inside 0..L*L that do not match the lattices (the ground and
+    top energies, shifted ones): the sweep keeps every threshold load inside the table
+    (the candidates of a decision lie within two rows of the current energy, and the
+    table has zero rows around the grid), flips that would leave the grid are rejected,
+    and lattices, energies and histogram equal the oracle's run on the same inputs."""
+    torch, M, C = env
+    for L, W, lay, seed in [(16, 64, 0, 31), (32, 100, 1, 32), (24, 40, 0, 33)]:
+        N = L * L
+        with M.Muca(L, W, seed, layout=lay) as m:
+            m.set_weights(weights(L, seed))
+            m.sweep(1, False)
+            r, b = raw_copy(torch, C, m, L, W, lay, seed)
+            r.t0 = N
+            e_true = m.get_energies()
+            bad = np.where(np.arange(W) % 3 == 0, 0, np.where(np.arange(W) % 3 == 1, N, (e_true + 37) % (N + 1)))
+            bad = bad.astype(np.int32)
+            b["energy"].copy_(torch.from_numpy(bad))
+            s, T = m.get_lattice(), m.get_table()
+            torch.cuda.synchronize()
+            M.muca_batch_sweep_noalloc([r], 2, True)
+            torch.cuda.synchronize()
+            buf = b["lattice"].cpu().numpy()
+            if lay == 1:
+                buf = buf.view(np.uint32 if L <= 32 else np.uint64)
+            got = from_layout(buf, L, lay, W)
+        eo = bad.copy()
+        Ho = orc.run(L, seed, s, eo, T, N, 2 * N, True)
+        assert int(b["err"].item()) == 0
+        assert np.array_equal(got, s), L
+        assert np.array_equal(b["energy"].cpu().numpy(), eo), L
+        assert np.array_equal(b["hist"].cpu().numpy().view(np.uint64), Ho), L
