@@ -14,7 +14,13 @@
 namespace muca {
 namespace {
 
-constexpr int kSiteChunk = 1024;   // attempts whose sites are drawn at once
+// Attempts whose sites are drawn at once: 32-byte records, half as many for 64-bit rows
+// so that the larger lattices keep their block size.
+template <typename RowT>
+__host__ __device__ constexpr int site_chunk()
+{
+    return sizeof(RowT) == 4 ? 1024 : 512;
+}
 constexpr int kSpare = 4;          // records past a chunk's end, read by the look-ahead
 constexpr uint32_t kCleanBit = 1u << 31;   // in the first record of a clean group (offset word)
 constexpr int kRandStride = 6;     // words per table row: thresholds of k = 0..4, histogram count
@@ -24,17 +30,28 @@ template <typename RowT>
 size_t random_smem_bytes_t(int L, int wpb, bool)
 {
     const size_t rows = (size_t)L * L + 1 + 2 * kRandGuard;
-    return align_up(rows * kRandStride * 4, 16) + (size_t)(kSiteChunk + kSpare) * 16 + (size_t)L * wpb * sizeof(RowT);
+    return align_up(rows * kRandStride * 4, 16) + (size_t)(site_chunk<RowT>() + kSpare) * 32 +
+           (size_t)L * wpb * sizeof(RowT);
 }
 
-// Spin s (0 / 1) of the site and its number k of antiparallel neighbours, from the rows
-// above, at and below it; w holds x, x - 1 and x + 1 (mod L) in its low three bytes.
 template <typename RowT>
-__device__ __forceinline__ void site_count(RowT U, RowT C, RowT D, uint32_t w, uint32_t &s, uint32_t &k)
+__device__ __forceinline__ RowT row_mask(uint32_t lo, uint32_t hi)
 {
-    const int x = (int)(w & 0xFFu), xl = (int)((w >> 8) & 0xFFu), xr = (int)((w >> 16) & 0xFFu);
-    s = bit_at(C, x);
-    k = (s ^ bit_at(U, x)) + (s ^ bit_at(D, x)) + (s ^ bit_at(C, xl)) + (s ^ bit_at(C, xr));
+    return sizeof(RowT) == 4 ? (RowT)lo : (RowT)(((unsigned long long)hi << 32) | lo);
+}
+
+__device__ __forceinline__ uint32_t popcount(uint32_t v) { return (uint32_t)__popc(v); }
+__device__ __forceinline__ uint32_t popcount(unsigned long long v) { return (uint32_t)__popcll(v); }
+
+// Number k of antiparallel neighbours of a site from the rows above (U), at (C) and
+// below (D) it; bx holds the site's bit x, mh bits x and x - 1 (mod L).  Bit i of
+// C ^ rot(C) compares columns i and i + 1 (mod L), so its bits x and x - 1 are the
+// right and left disagreements.
+template <typename RowT>
+__device__ __forceinline__ uint32_t site_count(RowT U, RowT C, RowT D, RowT bx, RowT mh, int L)
+{
+    const RowT rot = (C >> 1) | ((C & (RowT)1) << (L - 1));
+    return popcount((C ^ rot) & mh) + popcount((U ^ C) & bx) + popcount((D ^ C) & bx);
 }
 
 __device__ __forceinline__ uint32_t lds_word(uint32_t addr)
@@ -47,6 +64,63 @@ __device__ __forceinline__ uint32_t lds_word(uint32_t addr)
 __device__ __forceinline__ void hist_count(uint32_t E)
 {
     asm volatile("red.shared.add.u32 [%0+20], 1;" ::"r"(E));
+}
+
+// Bit rows of a warp's 32 walkers from the int8 [site][walker] layout, four rows at a
+// time (their 16-byte loads in flight together): lane j receives walker w0 + j.  All 32
+// walkers must exist and W % 16 == 0; L is a multiple of 4 up to 64.
+template <typename RowT>
+__device__ __forceinline__ void warp_load_rows(const int8_t *g, int64_t W, int64_t w0, int L, int y0, int lane,
+                                               RowT (&out)[4])
+{
+    uint4 va[4][2], vb[4][2];
+#pragma unroll
+    for (int r = 0; r < 4; ++r)
+#pragma unroll
+        for (int half = 0; half < 2; ++half) {
+            const int x = half * 32 + lane;
+            va[r][half] = vb[r][half] = make_uint4(0u, 0u, 0u, 0u);
+            if (x < L) {
+                const uint4 *p = reinterpret_cast<const uint4 *>(g + (size_t)((y0 + r) * L + x) * (size_t)W + (size_t)w0);
+                va[r][half] = p[0];
+                vb[r][half] = p[1];
+            }
+        }
+#pragma unroll
+    for (int r = 0; r < 4; ++r) {
+        RowT row = 0;
+#pragma unroll
+        for (int half = 0; half < 2; ++half) {
+            if (half * 32 >= L)   // uniform over the warp
+                break;
+            const uint4 u = va[r][half], v = vb[r][half];
+            uint32_t m = gather_signs(u.x) | (gather_signs(u.y) << 4) | (gather_signs(u.z) << 8) |
+                         (gather_signs(u.w) << 12) | (gather_signs(v.x) << 16) | (gather_signs(v.y) << 20) |
+                         (gather_signs(v.z) << 24) | (gather_signs(v.w) << 28);
+            m = warp_transpose32(m, lane);
+            row |= (RowT)m << (32 * half);
+        }
+        out[r] = row;
+    }
+}
+
+template <typename RowT>
+__device__ __forceinline__ void warp_store_row(int8_t *g, int64_t W, int64_t w0, int L, int y, int lane, RowT r)
+{
+#pragma unroll
+    for (int half = 0; half < 2; ++half) {
+        if (half * 32 >= L)   // uniform over the warp
+            break;
+        const uint32_t m = warp_transpose32((uint32_t)(r >> (32 * half)), lane);
+        const int x = half * 32 + lane;
+        if (x < L) {
+            uint4 *p = reinterpret_cast<uint4 *>(g + (size_t)(y * L + x) * (size_t)W + (size_t)w0);
+            p[0] = make_uint4(spread_signs(m & 15u), spread_signs((m >> 4) & 15u), spread_signs((m >> 8) & 15u),
+                              spread_signs((m >> 12) & 15u));
+            p[1] = make_uint4(spread_signs((m >> 16) & 15u), spread_signs((m >> 20) & 15u),
+                              spread_signs((m >> 24) & 15u), spread_signs(m >> 28));
+        }
+    }
 }
 
 template <typename RowT, int LAYOUT, bool RECORD>
@@ -62,10 +136,13 @@ __global__ void __launch_bounds__(256) random_sweep_kernel(const SweepArgs a)
     // table row r holds energy r - kRandGuard; the guard rows are zero (never accepted)
     uint32_t *sT = reinterpret_cast<uint32_t *>(smem);
     // per site of the chunk: byte offsets of the rows above (plus kCleanBit, see below),
-    // at and below it in a walker's column, and x | x_left << 8 | x_right << 16 | y << 24;
-    // shared by all walkers of the block
+    // at and below it in a walker's column, and x | y << 24; shared by all walkers of the
+    // block
     uint4 *sSite = reinterpret_cast<uint4 *>(smem + align_up((size_t)nrows * kRandStride * 4, 16));
-    RowT *sRows = reinterpret_cast<RowT *>(reinterpret_cast<unsigned char *>(sSite) + (size_t)(kSiteChunk + kSpare) * 16);
+    // per site: its bit and its bit plus the left neighbour's, as row masks (lo, hi words)
+    constexpr int kChunk = site_chunk<RowT>();
+    uint4 *sMask = sSite + (kChunk + kSpare);
+    RowT *sRows = reinterpret_cast<RowT *>(sMask + (kChunk + kSpare));
     const int tid = threadIdx.x;
     const int64_t w = (int64_t)blockIdx.x * wpb + tid;
     bool active = w < a.W;
@@ -77,13 +154,25 @@ __global__ void __launch_bounds__(256) random_sweep_kernel(const SweepArgs a)
     }
     RowT *col = sRows + tid;   // this walker's rows: col[y * wpb]
     unsigned char *cbytes = reinterpret_cast<unsigned char *>(col);
+    const int lane = tid & 31;
+    const int64_t w0 = w - lane;
+    // the whole warp exists and its 32 bytes per site are 16-byte aligned: uniform
+    const bool warp_full = LAYOUT == MUCA_LAYOUT_INT8 && w0 + 32 <= a.W && a.W % 16 == 0;
+    if (warp_full)
+        for (int y = 0; y < L; y += 4) {
+            RowT r4[4];
+            warp_load_rows<RowT>(reinterpret_cast<const int8_t *>(a.lattice), a.W, w0, L, y, lane, r4);
+#pragma unroll
+            for (int i = 0; i < 4; ++i)
+                col[(y + i) * wpb] = r4[i];
+        }
     int32_t e = 0;
     if (active) {
         if (LAYOUT == MUCA_LAYOUT_PACKED) {
             const RowT *g = reinterpret_cast<const RowT *>(a.lattice);
             for (int y = 0; y < L; ++y)
                 col[y * wpb] = g[(size_t)y * a.W + w];
-        } else {
+        } else if (!warp_full) {
             const int8_t *g = reinterpret_cast<const int8_t *>(a.lattice);
             for (int y = 0; y < L; ++y) {
                 RowT r = 0;
@@ -107,8 +196,8 @@ __global__ void __launch_bounds__(256) random_sweep_kernel(const SweepArgs a)
     const uint32_t wid = a.walker0 + (uint32_t)w;
     const uint64_t tend = a.t0 + a.n;
     const uint32_t rb = (uint32_t)wpb * (uint32_t)sizeof(RowT);   // bytes between rows of a column
-    for (uint64_t tc = a.t0; tc < tend; tc += kSiteChunk) {
-        const int m = tend - tc < (uint64_t)kSiteChunk ? (int)(tend - tc) : kSiteChunk;
+    for (uint64_t tc = a.t0; tc < tend; tc += kChunk) {
+        const int m = tend - tc < (uint64_t)kChunk ? (int)(tend - tc) : kChunk;
         __syncthreads();   // the previous chunk's sites are consumed (and the setup done)
         for (int j = tid; j < m; j += wpb) {
             const uint64_t t = tc + (uint64_t)j;
@@ -119,12 +208,16 @@ __global__ void __launch_bounds__(256) random_sweep_kernel(const SweepArgs a)
             const uint32_t i = __umulhi(u, (uint32_t)N);
             const int y = (int)(i / (uint32_t)L), x = (int)i - y * L;
             const int yu = (y == 0) ? L - 1 : y - 1, yd = (y == L - 1) ? 0 : y + 1;
-            const int xl = (x == 0) ? L - 1 : x - 1, xr = (x == L - 1) ? 0 : x + 1;
+            const int xl = (x == 0) ? L - 1 : x - 1;
             sSite[j] = make_uint4((uint32_t)yu * rb, (uint32_t)y * rb, (uint32_t)yd * rb,
-                                  (uint32_t)(x | (xl << 8) | (xr << 16) | (y << 24)));
+                                  (uint32_t)(x | (y << 24)));
+            const unsigned long long bx = 1ull << x, mh = bx | (1ull << xl);
+            sMask[j] = make_uint4((uint32_t)bx, (uint32_t)(bx >> 32), (uint32_t)mh, (uint32_t)(mh >> 32));
         }
-        if (tid < kSpare)   // look-ahead records past the chunk's last site: any valid rows
+        if (tid < kSpare) {   // look-ahead records past the chunk's last site: any valid rows
             sSite[m + tid] = make_uint4(0u, 0u, 0u, 0u);
+            sMask[m + tid] = make_uint4(0u, 0u, 0u, 0u);
+        }
         __syncthreads();
         // Groups of four attempts that share a Philox block start at t = 0 mod 4.  A group
         // is clean when none of its sites coincides with or neighbours an earlier site
@@ -155,16 +248,18 @@ __global__ void __launch_bounds__(256) random_sweep_kernel(const SweepArgs a)
         __syncthreads();
         if (!active)
             continue;
-        auto flip = [&](uint32_t off, uint32_t w, bool acc) {
-            atomicXor(reinterpret_cast<RowT *>(cbytes + off), acc ? (RowT)1 << (w & 0xFFu) : (RowT)0);
+        auto flip = [&](uint32_t off, RowT bx, bool acc) {
+            atomicXor(reinterpret_cast<RowT *>(cbytes + off), acc ? bx : (RowT)0);
+        };
+        auto count = [&](const uint4 &mk, RowT U, RowT C, RowT D) {
+            return site_count<RowT>(U, C, D, row_mask<RowT>(mk.x, mk.y), row_mask<RowT>(mk.z, mk.w), L);
         };
         // one attempt on rows read after every earlier flip
         auto single = [&](int jj, uint32_t r) {
-            const uint4 rc = sSite[jj];
-            uint32_t sx, k;
-            site_count(row(rc.x & ~kCleanBit), row(rc.y), row(rc.z), rc.w, sx, k);
+            const uint4 rc = sSite[jj], mk = sMask[jj];
+            const uint32_t k = count(mk, row(rc.x & ~kCleanBit), row(rc.y), row(rc.z));
             const bool acc = r < lds_word(E + 4u * k);
-            flip(rc.y, rc.w, acc);
+            flip(rc.y, row_mask<RowT>(mk.x, mk.y), acc);
             E = acc ? E + (2u - k) * kRowBytes : E;
             if (RECORD)
                 hist_count(E);
@@ -183,14 +278,15 @@ __global__ void __launch_bounds__(256) random_sweep_kernel(const SweepArgs a)
             single(j, word_at(words(t), (uint32_t)(t & 3)));
         if (m - j >= 4) {
             uint4 c0 = sSite[j], c1 = sSite[j + 1], c2 = sSite[j + 2], c3 = sSite[j + 3];
-            uint32_t kc0, kc1, kc2, kc3, sx;
-            site_count(row(c0.x & ~kCleanBit), row(c0.y), row(c0.z), c0.w, sx, kc0);
-            site_count(row(c1.x & ~kCleanBit), row(c1.y), row(c1.z), c1.w, sx, kc1);
-            site_count(row(c2.x & ~kCleanBit), row(c2.y), row(c2.z), c2.w, sx, kc2);
-            site_count(row(c3.x & ~kCleanBit), row(c3.y), row(c3.z), c3.w, sx, kc3);
+            uint4 b0 = sMask[j], b1 = sMask[j + 1], b2 = sMask[j + 2], b3 = sMask[j + 3];
+            uint32_t kc0 = count(b0, row(c0.x & ~kCleanBit), row(c0.y), row(c0.z));
+            uint32_t kc1 = count(b1, row(c1.x & ~kCleanBit), row(c1.y), row(c1.z));
+            uint32_t kc2 = count(b2, row(c2.x & ~kCleanBit), row(c2.y), row(c2.z));
+            uint32_t kc3 = count(b3, row(c3.x & ~kCleanBit), row(c3.y), row(c3.z));
             for (; m - j >= 4; j += 4, t += 4) {
                 // the next group's sites and rows, read before this group's flips
                 const uint4 n0 = sSite[j + 4], n1 = sSite[j + 5], n2 = sSite[j + 6], n3 = sSite[j + 7];
+                const uint4 p0 = sMask[j + 4], p1 = sMask[j + 5], p2 = sMask[j + 6], p3 = sMask[j + 7];
                 const RowT u0 = row(n0.x & ~kCleanBit), m0 = row(n0.y), d0r = row(n0.z);
                 const RowT u1 = row(n1.x & ~kCleanBit), m1 = row(n1.y), d1r = row(n1.z);
                 const RowT u2 = row(n2.x & ~kCleanBit), m2 = row(n2.y), d2r = row(n2.z);
@@ -205,24 +301,24 @@ __global__ void __launch_bounds__(256) random_sweep_kernel(const SweepArgs a)
                     const uint32_t T00 = lds_word(E + 4u * kc0);
                     const uint32_t T10 = lds_word(E + 4u * kc1), T11 = lds_word(E + s0 + 4u * kc1);
                     const bool a0 = q.x < T00;
-                    flip(c0.y, c0.w, a0);
+                    flip(c0.y, row_mask<RowT>(b0.x, b0.y), a0);
                     const uint32_t E1 = a0 ? E + s0 : E;
                     if (RECORD)
                         hist_count(E1);
                     const uint32_t T20 = lds_word(E1 + 4u * kc2), T21 = lds_word(E1 + s1 + 4u * kc2);
                     const bool a1 = q.y < (a0 ? T11 : T10);
-                    flip(c1.y, c1.w, a1);
+                    flip(c1.y, row_mask<RowT>(b1.x, b1.y), a1);
                     const uint32_t E2 = a1 ? E1 + s1 : E1;
                     if (RECORD)
                         hist_count(E2);
                     const uint32_t T30 = lds_word(E2 + 4u * kc3), T31 = lds_word(E2 + s2 + 4u * kc3);
                     const bool a2 = q.z < (a1 ? T21 : T20);
-                    flip(c2.y, c2.w, a2);
+                    flip(c2.y, row_mask<RowT>(b2.x, b2.y), a2);
                     const uint32_t E3 = a2 ? E2 + s2 : E2;
                     if (RECORD)
                         hist_count(E3);
                     const bool a3 = q.w < (a2 ? T31 : T30);
-                    flip(c3.y, c3.w, a3);
+                    flip(c3.y, row_mask<RowT>(b3.x, b3.y), a3);
                     E = a3 ? E3 + s3 : E3;
                     if (RECORD)
                         hist_count(E);
@@ -232,14 +328,18 @@ __global__ void __launch_bounds__(256) random_sweep_kernel(const SweepArgs a)
                     single(j + 2, q.z);
                     single(j + 3, q.w);
                 }
-                site_count(u0, m0, d0r, n0.w, sx, kc0);
-                site_count(u1, m1, d1r, n1.w, sx, kc1);
-                site_count(u2, m2, d2r, n2.w, sx, kc2);
-                site_count(u3, m3, d3r, n3.w, sx, kc3);
+                kc0 = count(p0, u0, m0, d0r);
+                kc1 = count(p1, u1, m1, d1r);
+                kc2 = count(p2, u2, m2, d2r);
+                kc3 = count(p3, u3, m3, d3r);
                 c0 = n0;
                 c1 = n1;
                 c2 = n2;
                 c3 = n3;
+                b0 = p0;
+                b1 = p1;
+                b2 = p2;
+                b3 = p3;
             }
         }
         for (; j < m; ++j, ++t)   // the tail of a launch that ends inside a Philox block
@@ -257,12 +357,15 @@ __global__ void __launch_bounds__(256) random_sweep_kernel(const SweepArgs a)
             if (v)
                 atomicAdd(&a.hist[i], (unsigned long long)v);
         }
+    if (warp_full)   // a walker flagged invalid above kept its rows unchanged
+        for (int y = 0; y < L; ++y)
+            warp_store_row<RowT>(reinterpret_cast<int8_t *>(a.lattice), a.W, w0, L, y, lane, col[y * wpb]);
     if (active) {
         if (LAYOUT == MUCA_LAYOUT_PACKED) {
             RowT *g = reinterpret_cast<RowT *>(a.lattice);
             for (int y = 0; y < L; ++y)
                 g[(size_t)y * a.W + w] = col[y * wpb];
-        } else {
+        } else if (!warp_full) {
             int8_t *g = reinterpret_cast<int8_t *>(a.lattice);
             for (int y = 0; y < L; ++y) {
                 const RowT r = col[y * wpb];
