@@ -468,8 +468,8 @@ def run_reference(args):
     sample_walkers = 2048
     lnW = np.zeros(N + 1)
     rates = []
-    for _ in range(args.warmup):
-        pass
+    for _ in range(args.warmup):   # untimed: process pool start-up and first-touch costs
+        cpu_baseline(lnW, sample_walkers)
     cores_used = 1
     for _ in range(args.steps):
         rate, cores_used, _ = cpu_baseline(lnW, sample_walkers)
