@@ -133,8 +133,10 @@ typedef struct {
  * Kullback-Leibler reference width of Eq. (6)), whether the whole range had been covered
  * (Eq. (7) then gives way to the growth rule) and the previous N_updates.  With
  * params.resume = 1 a run stopped by max_iterations or the deadline, or restored from a
- * checkpoint, continues the schedule as one uninterrupted call would have.  The batched
- * and served iterations and muca_iterate_device start afresh (they reject resume = 1). */
+ * checkpoint, continues the schedule as one uninterrupted call would have.
+ * muca_iterate_device and muca_batch_iterate (fixed-sweep schedule) keep and continue the
+ * same state (the previous range of the Kullback-Leibler reference); served requests
+ * start afresh (muca_server_submit rejects resume = 1). */
 
 /* Statistics of a weight iteration. */
 typedef struct {

@@ -595,8 +595,8 @@ int check_iteration_params(const muca_params &p, muca_t h)
         return fail(MUCA_EINVAL, "batched iteration supports the fixed-sweep schedule");
     if (p.stop_rule < MUCA_STOP_MIN_MEAN || p.stop_rule > MUCA_STOP_CHEBYSHEV || p.max_iterations < 1)
         return fail(MUCA_EINVAL, "bad stop rule or max_iterations");
-    if (p.resume)
-        return fail(MUCA_EINVAL, "batched iterations start afresh (resume = 0)");
+    if (p.resume != 0 && p.resume != 1)
+        return fail(MUCA_EINVAL, "resume must be 0 or 1");
     if (p.sweeps_per_iter * (uint64_t)h->N > 0xFFFFFFFFull / 256ull)
         return fail(MUCA_EINVAL, "sweeps_per_iter too large for one recording launch");
     if (h->t % (uint64_t)h->N != 0)
@@ -666,6 +666,10 @@ bool member_update(muca_t h, const muca_params &p, muca_stats &s)
             h->lnW[(size_t)e] -= muca::fp64::log((double)H[(size_t)e]);
     if (!visited_range(N, H, h->kl_lo, h->kl_hi))
         h->kl_lo = h->kl_hi = -1;
+    h->sched.prev_lo = h->kl_lo;
+    h->sched.prev_hi = h->kl_hi;
+    h->sched.prev_width = h->kl_lo >= 0 ? h->kl_hi - h->kl_lo + 1 : 0;
+    h->sched.upd_prev = p.sweeps_per_iter * (uint64_t)N;
     return s.iterations >= p.max_iterations;
 }
 
@@ -1218,8 +1222,8 @@ int muca_iterate_device(muca_t h, const muca_params *p_in, int32_t iterations_pe
         muca_default_params(&p);
     if (p.schedule != MUCA_SCHEDULE_SWEEPS)
         return fail(MUCA_EINVAL, "muca_iterate_device runs the fixed-sweep schedule only");
-    if (p.resume)
-        return fail(MUCA_EINVAL, "muca_iterate_device starts the iteration afresh (resume = 0)");
+    if (p.resume != 0 && p.resume != 1)
+        return fail(MUCA_EINVAL, "resume must be 0 or 1");
     if (h->reducer)
         return fail(MUCA_EINVAL, "muca_iterate_device cannot reduce histograms over instances");
     if (p.stop_rule < MUCA_STOP_MIN_MEAN || p.stop_rule > MUCA_STOP_CHEBYSHEV)
@@ -1247,8 +1251,8 @@ int muca_iterate_device(muca_t h, const muca_params *p_in, int32_t iterations_pe
     // the first table and the weights from the host; the state zeroed
     MUCA_CUDA(cudaStreamSynchronize(h->stream), "stream synchronize");
     std::memset(h->h_iter, 0, sizeof(muca::IterState));
-    h->h_iter->prev_lo = -1;
-    h->h_iter->prev_hi = -1;
+    h->h_iter->prev_lo = p.resume ? h->sched.prev_lo : -1;
+    h->h_iter->prev_hi = p.resume ? h->sched.prev_hi : -1;
     MUCA_CUDA(cudaMemcpyAsync(h->d_iter, h->h_iter, sizeof(muca::IterState), cudaMemcpyHostToDevice, h->stream),
               "iteration state upload");
     MUCA_CUDA(cudaMemcpyAsync(h->d_lnW, h->lnW.data(), nb * sizeof(double), cudaMemcpyHostToDevice, h->stream),
@@ -1293,6 +1297,12 @@ int muca_iterate_device(muca_t h, const muca_params *p_in, int32_t iterations_pe
               "weights read");
     MUCA_CUDA(cudaStreamSynchronize(h->stream), "stream synchronize");
     const bool flat = st.done == 1u;
+    if (st.iterations > (flat ? 1 : 0)) {   // at least one weight update: the state the host loop keeps
+        h->sched.prev_lo = st.prev_lo;
+        h->sched.prev_hi = st.prev_hi;
+        h->sched.prev_width = st.prev_lo >= 0 ? st.prev_hi - st.prev_lo + 1 : 0;
+        h->sched.upd_prev = n_upd;
+    }
     if (stats) {
         stats->iterations = st.iterations;
         stats->converged = flat ? 1 : 0;
@@ -1797,8 +1807,10 @@ int muca_batch_iterate(muca_batch_t b, const muca_params *p_in, muca_stats *stat
     const auto start = std::chrono::steady_clock::now();
     std::vector<muca_stats> st(n);
     std::memset(st.data(), 0, sizeof(muca_stats) * n);
-    for (muca_t h : b->inst)
-        h->kl_lo = h->kl_hi = -1;
+    for (muca_t h : b->inst) {
+        h->kl_lo = p.resume ? h->sched.prev_lo : -1;
+        h->kl_hi = p.resume ? h->sched.prev_hi : -1;
+    }
     std::vector<int32_t> active(n);
     for (size_t i = 0; i < n; ++i)
         active[i] = (int32_t)i;

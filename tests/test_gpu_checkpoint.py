@@ -143,3 +143,48 @@ def test_iteration_resumes_across_calls_and_checkpoints(muca_mod, tmp_path, sche
         assert fresh[0][:2] != whole[k][:2]      # N_therm, N_updates of w = 10 again
     else:
         assert fresh[0][:2] == whole[k][:2]      # fixed sweeps; only the KL reference differs
+
+
+@pytest.mark.parametrize("mode", ["device", "batch"])
+def test_device_and_batched_iterations_resume(muca_mod, tmp_path, mode):
+    """The device-side and the batched iteration (fixed sweeps, Kullback-Leibler stop of
+    Eq. (6), whose reference width comes from the previous iteration's range) cut by
+    max_iterations and continued with params.resume, also after a checkpoint, equal one
+    uninterrupted run: iterations, stop metric, weights and attempt counter."""
+    M = muca_mod
+    L, seeds = 8, (4, 5)
+    kw = dict(stop_rule=M.MUCA_STOP_KL, flat_threshold=0.01, therm_sweeps=31, sweeps_per_iter=100)
+
+    def run(ms, p):
+        if mode == "device":
+            return [m.iterate_device(p, 3) for m in ms]
+        with M.Batch(ms) as b:
+            return b.iterate_until_flat(p)[1]
+
+    def fresh():
+        return [M.Muca(L, 128, s) for s in seeds]
+
+    whole = fresh()
+    st = run(whole, M.make_params(max_iterations=3000, **kw))
+    ref = [(m.get_weights(), m.info()[2]) for m in whole]
+    assert all(s.converged and s.iterations >= 4 for s in st)
+    for m in whole:
+        m.close()
+    k = min(s.iterations for s in st) // 2
+    path = [str(tmp_path / f"cut{i}.muca") for i in range(len(seeds))]
+    for restore in (False, True):
+        ms = fresh()
+        first = run(ms, M.make_params(max_iterations=k, **kw))
+        assert all(not s.converged and s.iterations == k for s in first)
+        if restore:
+            for m, pth in zip(ms, path):
+                m.save(pth)
+                m.close()
+            ms = [M.Muca.load(pth) for pth in path]
+        second = run(ms, M.make_params(max_iterations=3000, resume=True, **kw))
+        for m, s_all, s2, (w, t) in zip(ms, st, second, ref):
+            assert s2.converged and k + s2.iterations == s_all.iterations
+            assert s2.last_metric == s_all.last_metric
+            assert np.array_equal(m.get_weights(), w) and m.info()[2] == t
+        for m in ms:
+            m.close()
