@@ -1,5 +1,5 @@
-// muca_internal.h - launch interface between the host library (muca_api.cu) and the
-// device kernels (muca_kernels.cu).  Not part of the public ABI.
+// muca_internal.h - launch interface between the host library (muca_api*.cu) and the
+// device kernels (muca_kernels.cu and the other kernel files).  Not part of the public ABI.
 #pragma once
 
 #include <cstddef>
