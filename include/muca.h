@@ -311,6 +311,17 @@ int muca_iterate_device(muca_t h, const muca_params *p, int32_t iterations_per_s
 int muca_build_table(int32_t L, const double *lnW, size_t n_bins, uint32_t *T_out);
 int muca_update_weights(int32_t L, double *lnW, const uint64_t *H, size_t n_bins);
 
+/* The three flatness measures of a histogram H[n_bins] (n_bins = L*L + 1), host FP64 as
+ * the iteration computes them: *min_over_mean = min H / mean H over the accessible
+ * energies; *kl = d_k of Eq. (6) with the reference width taken from the union of
+ * [prev_lo, prev_hi] (the previous iteration's visited range, prev_lo = -1 for none) and
+ * the visited range of H; *chebyshev = d_c of Eq. (A.1); *lo, *hi = the visited range of H
+ * (-1, -1 when empty).  Every output may be NULL.  For per-iteration logs (the
+ * convergence traces of App. A).  Errors: MUCA_EINVAL (L as in muca_create, wrong
+ * n_bins, NULL H, prev_hi < prev_lo or outside the grid when prev_lo >= 0). */
+int muca_flatness(int32_t L, const uint64_t *H, size_t n_bins, int32_t prev_lo, int32_t prev_hi,
+                  double *min_over_mean, double *kl, double *chebyshev, int32_t *lo, int32_t *hi);
+
 /* Production run (Sec. 3.3) with the current weights: therm_sweeps unrecorded sweeps,
  * zero H, n_sweeps recorded sweeps, then ln g(e) = ln H(e) - ln W(e) on visited energies
  * shifted so that sum_e exp(ln g(e)) = 2^N; unvisited energies get -inf.  H_out (may

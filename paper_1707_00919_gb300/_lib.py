@@ -115,6 +115,9 @@ SIGNATURES = {
     "muca_get_site_order": (ctypes.c_int, [_H, _P(ctypes.c_int32)]),
     "muca_build_table": (ctypes.c_int, [ctypes.c_int32, _P(ctypes.c_double), ctypes.c_size_t, _P(ctypes.c_uint32)]),
     "muca_update_weights": (ctypes.c_int, [ctypes.c_int32, _P(ctypes.c_double), _P(ctypes.c_uint64), ctypes.c_size_t]),
+    "muca_flatness": (ctypes.c_int, [ctypes.c_int32, _P(ctypes.c_uint64), ctypes.c_size_t, ctypes.c_int32,
+                                     ctypes.c_int32, _P(ctypes.c_double), _P(ctypes.c_double), _P(ctypes.c_double),
+                                     _P(ctypes.c_int32), _P(ctypes.c_int32)]),
     "muca_destroy": (ctypes.c_int, [_H]),
     "muca_set_stream": (ctypes.c_int, [_H, ctypes.c_void_p]),
     "muca_set_allocator": (ctypes.c_int, [ALLOC_FN, RELEASE_FN, ctypes.c_void_p]),

@@ -252,6 +252,33 @@ int muca_update_weights(int32_t L, double *lnW, const uint64_t *H, size_t n_bins
     return MUCA_OK;
 }
 
+int muca_flatness(int32_t L, const uint64_t *H, size_t n_bins, int32_t prev_lo, int32_t prev_hi,
+                  double *min_over_mean_out, double *kl_out, double *chebyshev_out, int32_t *lo_out, int32_t *hi_out)
+{
+    if (L < 4 || L > 64 || L % 4 != 0)
+        return fail(MUCA_EINVAL, "L = %d: must be a multiple of 4 in [4, 64]", L);
+    const int32_t N = L * L;
+    if (!H || n_bins != (size_t)N + 1)
+        return fail(MUCA_EINVAL, "need a histogram of %d bins", N + 1);
+    if (prev_lo >= 0 && (prev_hi < prev_lo || prev_hi > N))
+        return fail(MUCA_EINVAL, "previous range [%d, %d] is not inside [0, %d]", prev_lo, prev_hi, N);
+    const std::vector<uint64_t> h(H, H + n_bins);
+    const int32_t plo = prev_lo >= 0 ? prev_lo : -1, phi = prev_lo >= 0 ? prev_hi : -1;
+    if (min_over_mean_out)
+        *min_over_mean_out = min_over_mean(N, h);
+    if (kl_out)
+        *kl_out = kullback_leibler(N, h, (double)kl_support(N, plo, phi, h));
+    if (chebyshev_out)
+        *chebyshev_out = chebyshev(N, h);
+    int32_t lo, hi;
+    visited_range(N, h, lo, hi);
+    if (lo_out)
+        *lo_out = lo;
+    if (hi_out)
+        *hi_out = hi;
+    return MUCA_OK;
+}
+
 int muca_iterate_device(muca_t h, const muca_params *p_in, int32_t iterations_per_sync, muca_stats *stats)
 {
     int rc = validate(h);

@@ -254,6 +254,48 @@ def muca_update_weights(L: int, lnW: np.ndarray, H) -> None:
     _check(C.load().muca_update_weights(L, _p(lnW, ctypes.c_double), _p(h, ctypes.c_uint64), lnW.size))
 
 
+def muca_flatness(L: int, H, prev_range: tuple[int, int] = (-1, -1)) -> dict:
+    """min/mean, d_k (Eq. 6, reference width from prev_range and H's range) and d_c
+    (Eq. A.1) of a histogram, and its visited range."""
+    h = np.ascontiguousarray(H, dtype=np.uint64)
+    mm, kl, dc = ctypes.c_double(), ctypes.c_double(), ctypes.c_double()
+    lo, hi = ctypes.c_int32(), ctypes.c_int32()
+    _check(C.load().muca_flatness(L, _p(h, ctypes.c_uint64), h.size, prev_range[0], prev_range[1], ctypes.byref(mm),
+                                  ctypes.byref(kl), ctypes.byref(dc), ctypes.byref(lo), ctypes.byref(hi)))
+    return {"min_over_mean": mm.value, "kl": kl.value, "chebyshev": dc.value, "range": (lo.value, hi.value)}
+
+
+class IterationLog:
+    """Per-iteration JSON lines for Muca.set_iteration_observer: iteration, visited
+    width w, N_therm and N_updates (attempts per walker), the three flatness measures,
+    the stop metric, wall time and attempts per second since the previous line."""
+
+    def __init__(self, path: str, L: int, n_walkers: int):
+        import time
+        self._time = time.perf_counter
+        self.L, self.W = L, n_walkers
+        self.f = open(path, "w")
+        self.prev = (-1, -1)
+        self.t0 = self.t_last = self._time()
+
+    def __call__(self, iteration, H, metric, n_therm, n_updates):
+        import json
+        now = self._time()
+        fl = muca_flatness(self.L, H, self.prev)
+        lo, hi = fl["range"]
+        rec = {"iteration": int(iteration), "w": hi - lo + 1 if lo >= 0 else 0, "n_therm": int(n_therm),
+               "n_updates": int(n_updates), "min_over_mean": fl["min_over_mean"], "d_k": fl["kl"],
+               "d_c": fl["chebyshev"], "stop_metric": float(metric), "seconds": now - self.t0,
+               "attempts_per_s": self.W * (n_therm + n_updates) / max(now - self.t_last, 1e-12)}
+        self.f.write(json.dumps(rec) + "\n")
+        self.f.flush()
+        self.prev = (lo, hi) if lo >= 0 else (-1, -1)
+        self.t_last = now
+
+    def close(self) -> None:
+        self.f.close()
+
+
 def muca_production(h, therm_sweeps: int, n_sweeps: int, n_bins: int):
     H = np.zeros(n_bins, dtype=np.uint64)
     g = np.zeros(n_bins, dtype=np.float64)

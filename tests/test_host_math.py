@@ -64,3 +64,49 @@ def test_host_helpers_reject_bad_arguments(mm):
         mm.muca_build_table(4, bad)
     with pytest.raises(mm.MucaError):
         mm.muca_update_weights(4, np.zeros(16), np.zeros(16, dtype=np.uint64))
+
+
+def _kl_support(orc, L, prev, H):
+    import ctypes
+    h = np.ascontiguousarray(H, dtype=np.uint64)
+    return orc.lib().orc_kl_support(L, prev[0], prev[1], h.ctypes.data_as(ctypes.POINTER(ctypes.c_uint64)))
+
+
+@pytest.mark.parametrize("L", [4, 8, 32, 64])
+def test_flatness_measures_match_oracle(mm, orc, L):
+    """min/mean, d_k of Eq. (6) with the reading-R7 reference width, d_c of Eq. (A.1) and
+    the visited range, bit for bit against the oracle, on histograms with gaps, a single
+    bin, an empty one and flat ones, with and without a previous range."""
+    N = L * L
+    rng = np.random.default_rng(L)
+    cases = []
+    for _ in range(6):
+        H = rng.integers(0, 1000, N + 1).astype(np.uint64)
+        H[rng.random(N + 1) < 0.3] = 0
+        cases.append(H)
+    one = np.zeros(N + 1, np.uint64)
+    one[N // 2] = 7
+    flat = np.full(N + 1, 50, np.uint64)
+    flat[[1, N - 1]] = 0
+    cases += [one, flat, np.zeros(N + 1, np.uint64)]
+    for H in cases:
+        for prev in [(-1, -1), (0, N // 3), (N // 4, N)]:
+            got = mm.muca_flatness(L, H, prev)
+            q = _kl_support(orc, L, prev, H)
+            nz = np.nonzero(H)[0]
+            assert got["range"] == ((int(nz[0]), int(nz[-1])) if nz.size else (-1, -1))
+            assert got["min_over_mean"] == orc.min_over_mean(L, H)
+            assert got["chebyshev"] == orc.chebyshev(L, H)
+            assert got["kl"] == orc.kullback_leibler(L, H, float(q))
+
+
+def test_flatness_rejects_bad_input(mm):
+    N = 64
+    with pytest.raises(mm.MucaError):
+        mm.muca_flatness(8, np.zeros(N, np.uint64))
+    with pytest.raises(mm.MucaError):
+        mm.muca_flatness(6, np.zeros(37, np.uint64))
+    with pytest.raises(mm.MucaError):
+        mm.muca_flatness(8, np.zeros(N + 1, np.uint64), (10, 5))
+    with pytest.raises(mm.MucaError):
+        mm.muca_flatness(8, np.zeros(N + 1, np.uint64), (10, N + 1))
