@@ -107,3 +107,30 @@ def test_order_arguments_and_batch_refusal(muca_mod):
         m.site_order = M.MUCA_ORDER_RANDOM
         with pytest.raises(M.MucaError):
             M.Batch([m])
+
+
+def test_full_size_sampled_walkers(muca_mod, orc):
+    """The random-order measurement of bench.py at full size (L = 32, 16384 walkers,
+    perfect weights, 3 thermalization and 2 recorded sweeps): sampled walkers, at warp
+    and block edges and inside, equal the oracle walker by walker; the histogram counts
+    every recorded attempt."""
+    from conftest import load_exact_ln_dos
+    M = muca_mod
+    L, W, seed = 32, 16384, 1
+    N = L * L
+    lng = load_exact_ln_dos(L)
+    lnW = np.where(np.isfinite(lng), -lng, 0.0)
+    with M.Muca(L, W, seed) as m:
+        m.site_order = M.MUCA_ORDER_RANDOM
+        m.set_weights(lnW)
+        m.sweep(3, False)
+        m.reset_histogram()
+        m.sweep(2, True)
+        H, e, lat = m.get_histogram(), m.get_energies(), m.get_lattice()
+    assert int(H.sum()) == W * 2 * N
+    T = orc.build_table(L, lnW)
+    for w in [0, 1, 31, 32, 127, 128, 5000, 9999, W - 1]:
+        s, eo = orc.init(L, seed, 1, walker0=w)
+        orc.run(L, seed, s, eo, T, 0, 3 * N, False, walker0=w, site_order=1)
+        orc.run(L, seed, s, eo, T, 3 * N, 2 * N, True, walker0=w, site_order=1)
+        assert np.array_equal(lat[w], s[0]) and e[w] == eo[0], w
