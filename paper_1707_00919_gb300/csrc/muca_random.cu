@@ -291,8 +291,16 @@ __global__ void __launch_bounds__(256) random_sweep_kernel(const SweepArgs a)
                 const RowT u1 = row(n1.x & ~kCleanBit), m1 = row(n1.y), d1r = row(n1.z);
                 const RowT u2 = row(n2.x & ~kCleanBit), m2 = row(n2.y), d2r = row(n2.z);
                 const RowT u3 = row(n3.x & ~kCleanBit), m3 = row(n3.y), d3r = row(n3.z);
-                const uint4 q = words(t);
+                // the next group's counts; computed inside each branch below, so that the
+                // scheduler can place them (and the Philox rounds) between the decisions
+                auto next_counts = [&]() {
+                    kc0 = count(p0, u0, m0, d0r);
+                    kc1 = count(p1, u1, m1, d1r);
+                    kc2 = count(p2, u2, m2, d2r);
+                    kc3 = count(p3, u3, m3, d3r);
+                };
                 if (c0.x & kCleanBit) {
+                    const uint4 q = words(t);
                     // Each decision takes one of two thresholds loaded one attempt
                     // ahead (the previous attempt rejected / flipped); the counts are
                     // known for the whole group.
@@ -322,16 +330,15 @@ __global__ void __launch_bounds__(256) random_sweep_kernel(const SweepArgs a)
                     E = a3 ? E3 + s3 : E3;
                     if (RECORD)
                         hist_count(E);
+                    next_counts();
                 } else {
+                    const uint4 q = words(t);
                     single(j, q.x);
                     single(j + 1, q.y);
                     single(j + 2, q.z);
                     single(j + 3, q.w);
+                    next_counts();
                 }
-                kc0 = count(p0, u0, m0, d0r);
-                kc1 = count(p1, u1, m1, d1r);
-                kc2 = count(p2, u2, m2, d2r);
-                kc3 = count(p3, u3, m3, d3r);
                 c0 = n0;
                 c1 = n1;
                 c2 = n2;
