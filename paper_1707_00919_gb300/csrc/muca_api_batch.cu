@@ -546,10 +546,10 @@ int muca_batch_sweep_noalloc(const muca_raw_instance *instances, int32_t n, uint
             return fail(MUCA_EINVAL, "instance %d: %llu sweeps exceed one launch (at most %llu recorded attempts per walker)",
                         i, (unsigned long long)n_sweeps, (unsigned long long)(0xFFFFFFFFull / 256ull));
         int32_t wpb = 256;
-        while (wpb > 32 && muca::full_smem_bytes(r.L, wpb, true) > limit)
+        while (wpb > 32 && muca::full_smem_bytes(r.L, wpb, true, true) > limit)
             wpb -= 32;
         wpbs[i] = wpb;
-        smem = std::max(smem, muca::full_smem_bytes(r.L, wpb, true));
+        smem = std::max(smem, muca::full_smem_bytes(r.L, wpb, true, true));
         muca::SweepArgs &d = descs[i];
         d.L = r.L;
         d.layout = r.layout;

@@ -440,8 +440,10 @@ __device__ __forceinline__ void process_row(const uint32_t (&U)[L / 8], uint32_t
 // `a` (threads tid >= wpb idle), all of the launch's whole sweeps.  Shared memory:
 // the table, then the rows of the wpb walkers.  Every thread of the block calls it.
 // The layout only changes the loads and stores around the sweeps; callers with a
-// compile-time layout get it folded, the batched kernels pass it at run time.
-template <int L, bool RECORD, bool PARTIAL = false>
+// compile-time layout get it folded, the batched kernels pass it at run time.  GUARD
+// adds kTableGuard zero rows on both sides of the table, for energies that come from the
+// caller and need not match the lattices (the library's own energies always do).
+template <int L, bool RECORD, bool PARTIAL = false, bool GUARD = false>
 __device__ __forceinline__ void sweep_block(const SweepArgs &a, int64_t wbase, int wpb, unsigned char *smem,
                                             const int LAYOUT)
 {
@@ -455,7 +457,8 @@ __device__ __forceinline__ void sweep_block(const SweepArgs &a, int64_t wbase, i
     const int nthr = blockDim.x;
     uint32_t *sTab = reinterpret_cast<uint32_t *>(smem);
     const int tid = threadIdx.x;
-    constexpr int NR = NB + 2 * kTableGuard;   // table rows: energies -2 .. N + 2
+    constexpr int G = GUARD ? kTableGuard : 0;
+    constexpr int NR = NB + 2 * G;   // table rows: energies -G .. N + G
     const SmemRows<L> rows{smem + align_up((size_t)NR * kTableStride * 4, 16), wpb, tid};
     const int lane = tid & 31;
     const bool in_item = tid < wpb;
@@ -464,10 +467,17 @@ __device__ __forceinline__ void sweep_block(const SweepArgs &a, int64_t wbase, i
     bool active = in_item && w < a.W;
     const bool warp_full = in_item && (w0 + 32 <= a.W) && (a.W % 16 == 0);
 
-    for (int i = tid; i < NR * kTableStride; i += nthr) {
-        const int r = i / kTableStride, k = i - r * kTableStride;
-        const int e = r - kTableGuard;
-        sTab[i] = (k < 5 && e >= 0 && e <= N) ? a.table[e * 5 + k] : 0u;
+    if (GUARD) {
+        for (int i = tid; i < NR * kTableStride; i += nthr) {
+            const int r = i / kTableStride, k = i - r * kTableStride;
+            const int e = r - G;
+            sTab[i] = (k < 5 && e >= 0 && e <= N) ? a.table[e * 5 + k] : 0u;
+        }
+    } else {
+        for (int i = tid; i < NB * kTableStride; i += nthr) {
+            const int e = i / kTableStride, k = i - e * kTableStride;
+            sTab[i] = k < 5 ? a.table[e * 5 + k] : 0u;
+        }
     }
 
     if (LAYOUT == MUCA_LAYOUT_PACKED) {
@@ -503,7 +513,7 @@ __device__ __forceinline__ void sweep_block(const SweepArgs &a, int64_t wbase, i
 
     if (active) {
         const PhiloxKeys pk = make_keys(a.seed, a.walker0 + (uint32_t)w);
-        const uint32_t tbase = (uint32_t)__cvta_generic_to_shared(sTab) + kTableGuard * kTableStride * 4u;
+        const uint32_t tbase = (uint32_t)__cvta_generic_to_shared(sTab) + G * kTableStride * 4u;
         uint32_t U[NW], C[NW], D[NW];
         uint32_t E = tbase + (uint32_t)e * (4u * kTableStride);
         if (!PARTIAL) {
@@ -572,7 +582,7 @@ __device__ __forceinline__ void sweep_block(const SweepArgs &a, int64_t wbase, i
     __syncthreads();
     if (RECORD)
         for (int i = tid; i < NB; i += nthr) {
-            const uint32_t v = sTab[(i + kTableGuard) * kTableStride + kHistSlot];
+            const uint32_t v = sTab[(i + G) * kTableStride + kHistSlot];
             if (v)
                 atomicAdd(&a.hist[i], (unsigned long long)v);
         }
@@ -597,10 +607,10 @@ __device__ __forceinline__ void sweep_block(const SweepArgs &a, int64_t wbase, i
 }
 
 // A batched work item: the whole-sweep body of the item's instance.
-template <int L, bool RECORD>
+template <int L, bool RECORD, bool GUARD = false>
 __device__ __forceinline__ void batch_item(const SweepArgs &a, const BatchItem &it, unsigned char *smem)
 {
-    sweep_block<L, RECORD>(a, it.wbase, it.wpb, smem, a.layout);
+    sweep_block<L, RECORD, false, GUARD>(a, it.wbase, it.wpb, smem, a.layout);
 }
 
 }  // namespace

@@ -13,9 +13,10 @@ namespace muca {
 // energy, thresholds in words 0..4, the block's histogram count in word kHistSlot.
 constexpr int kTableStride = 7;
 constexpr int kHistSlot = 5;
-// Zero rows below energy 0 and above N: the threshold candidates loaded ahead of a
-// decision lie within two rows of the current energy, so they stay inside the table
-// even for energies that do not match the lattice.
+// Zero rows below energy 0 and above N for the allocation-free entry point, whose
+// energies come from the caller: the threshold candidates loaded ahead of a decision lie
+// within two rows of the current energy, so they stay inside the table even for
+// energies that do not match the lattices.
 constexpr int kTableGuard = 2;
 
 // Device error word bits.
@@ -74,7 +75,7 @@ constexpr int kBatchThreads = 256;   // threads per block of the batched kernel
 size_t sweep_smem_bytes(int L, int walkers_per_block, bool record);
 
 // Shared memory bytes of the whole-sweep kernel (eight thresholds per energy).
-size_t full_smem_bytes(int L, int walkers_per_block, bool record);
+size_t full_smem_bytes(int L, int walkers_per_block, bool record, bool guard = false);
 
 // Largest dynamic shared memory a block may use on this device (bytes).
 size_t sweep_smem_limit();

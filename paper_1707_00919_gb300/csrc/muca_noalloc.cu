@@ -51,12 +51,12 @@ __global__ void __launch_bounds__(256, 1) batch_noalloc_kernel(const unsigned ch
         it.wpb = wpbs[i];
         it.wbase = wbase;
         switch (a.L) {
-        case 8: batch_item<8, RECORD>(a, it, smem); break;
-        case 16: batch_item<16, RECORD>(a, it, smem); break;
-        case 24: batch_item<24, RECORD>(a, it, smem); break;
-        case 32: batch_item<32, RECORD>(a, it, smem); break;
-        case 48: batch_item<48, RECORD>(a, it, smem); break;
-        case 64: batch_item<64, RECORD>(a, it, smem); break;
+        case 8: batch_item<8, RECORD, true>(a, it, smem); break;
+        case 16: batch_item<16, RECORD, true>(a, it, smem); break;
+        case 24: batch_item<24, RECORD, true>(a, it, smem); break;
+        case 32: batch_item<32, RECORD, true>(a, it, smem); break;
+        case 48: batch_item<48, RECORD, true>(a, it, smem); break;
+        case 64: batch_item<64, RECORD, true>(a, it, smem); break;
         default: break;
         }
     }
