@@ -474,7 +474,10 @@ int muca_server_totals(muca_server_t s, uint64_t *walker_attempts, double *secon
  * lattice in `layout`, energy indices int32[n_walkers], thresholds uint32[(L*L+1)*5]
  * (as muca_get_table returns them), histogram uint64[L*L+1] (added to), error word
  * uint32 (bits OR-ed in, 0 = fine).  t0 is the attempt counter of the first attempt and
- * must lie on a sweep boundary (a multiple of L*L). */
+ * must lie on a sweep boundary (a multiple of L*L).  A walker whose energy index lies
+ * outside 0..L*L sets bit 0 of the error word and is left unchanged; an index inside
+ * that range that does not match the walker's lattice is used as given (flips whose
+ * target energy leaves the grid are rejected), as the CPU reference does. */
 typedef struct {
     int32_t L;                   /* one of 8, 16, 24, 32, 48, 64                           */
     int32_t layout;              /* MUCA_LAYOUT_INT8 or MUCA_LAYOUT_PACKED                 */
