@@ -477,7 +477,7 @@ int muca_server_totals(muca_server_t s, uint64_t *walker_attempts, double *secon
  * must lie on a sweep boundary (a multiple of L*L).  A walker whose energy index lies
  * outside 0..L*L sets bit 0 of the error word and is left unchanged; an index inside
  * that range that does not match the walker's lattice is used as given (flips whose
- * target energy leaves the grid are rejected), as the CPU reference does. */
+ * target energy leaves the grid are rejected: their thresholds are 0). */
 typedef struct {
     int32_t L;                   /* one of 8, 16, 24, 32, 48, 64                           */
     int32_t layout;              /* MUCA_LAYOUT_INT8 or MUCA_LAYOUT_PACKED                 */
