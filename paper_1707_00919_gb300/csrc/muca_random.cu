@@ -46,11 +46,12 @@ __device__ __forceinline__ uint32_t popcount(unsigned long long v) { return (uin
 // Number k of antiparallel neighbours of a site from the rows above (U), at (C) and
 // below (D) it; bx holds the site's bit x, mh bits x and x - 1 (mod L).  Bit i of
 // C ^ rot(C) compares columns i and i + 1 (mod L), so its bits x and x - 1 are the
-// right and left disagreements.
-template <typename RowT>
+// right and left disagreements.  WIDE: L fills the row word, so rot is a plain rotation.
+template <typename RowT, bool WIDE>
 __device__ __forceinline__ uint32_t site_count(RowT U, RowT C, RowT D, RowT bx, RowT mh, int L)
 {
-    const RowT rot = (C >> 1) | ((C & (RowT)1) << (L - 1));
+    constexpr int kBits = 8 * (int)sizeof(RowT);
+    const RowT rot = WIDE ? (RowT)((C >> 1) | (C << (kBits - 1))) : (RowT)((C >> 1) | ((C & (RowT)1) << (L - 1)));
     return popcount((C ^ rot) & mh) + popcount((U ^ C) & bx) + popcount((D ^ C) & bx);
 }
 
@@ -123,7 +124,7 @@ __device__ __forceinline__ void warp_store_row(int8_t *g, int64_t W, int64_t w0,
     }
 }
 
-template <typename RowT, int LAYOUT, bool RECORD>
+template <typename RowT, int LAYOUT, bool RECORD, bool WIDE>
 __global__ void __launch_bounds__(256) random_sweep_kernel(const SweepArgs a)
 {
     extern __shared__ __align__(16) unsigned char smem[];
@@ -252,7 +253,7 @@ __global__ void __launch_bounds__(256) random_sweep_kernel(const SweepArgs a)
             atomicXor(reinterpret_cast<RowT *>(cbytes + off), acc ? bx : (RowT)0);
         };
         auto count = [&](const uint4 &mk, RowT U, RowT C, RowT D) {
-            return site_count<RowT>(U, C, D, row_mask<RowT>(mk.x, mk.y), row_mask<RowT>(mk.z, mk.w), L);
+            return site_count<RowT, WIDE>(U, C, D, row_mask<RowT>(mk.x, mk.y), row_mask<RowT>(mk.z, mk.w), L);
         };
         // one attempt on rows read after every earlier flip
         auto single = [&](int jj, uint32_t r) {
@@ -388,7 +389,8 @@ template <typename RowT, int LAYOUT, bool RECORD>
 cudaError_t launch_random_t(const SweepArgs &a, int wpb, cudaStream_t s)
 {
     const size_t smem = random_smem_bytes_t<RowT>(a.L, wpb, RECORD);
-    auto kern = random_sweep_kernel<RowT, LAYOUT, RECORD>;
+    auto kern = a.L == 8 * (int)sizeof(RowT) ? random_sweep_kernel<RowT, LAYOUT, RECORD, true>
+                                              : random_sweep_kernel<RowT, LAYOUT, RECORD, false>;
     if (smem > 48 * 1024) {
         const cudaError_t err = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         if (err != cudaSuccess)
