@@ -98,3 +98,26 @@ def test_bench_plumbing_two_ranks(tmp_path):
         ws, rank, local, value = (tmp_path / f"max_{r}.txt").read_text().split()
         assert (int(ws), int(rank), int(local)) == (2, r, r)
         assert float(value) == 2.5           # every rank sees the slowest rank's time
+
+
+def test_reference_arm_json_line():
+    """`bench.py --impl reference` (the oracle timed on the host cores, no GPU) prints one
+    JSON line with the contract's keys: metric, value, unit, steps, warmup, the oracle as
+    cpu_baseline (kind, cores, sample) and an e2e object without host-device traffic."""
+    import json
+    import subprocess
+    import sys
+    root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+    env = {k: v for k, v in os.environ.items() if k not in ("WORLD_SIZE", "RANK", "LOCAL_RANK")}
+    r = subprocess.run([sys.executable, os.path.join(root, "bench.py"), "--impl", "reference", "--steps", "1",
+                        "--warmup", "1"], capture_output=True, text=True, timeout=600, cwd=root, env=env)
+    assert r.returncode == 0, r.stderr[-2000:]
+    lines = [ln for ln in r.stdout.splitlines() if ln.startswith("{")]
+    assert len(lines) == 1
+    d = json.loads(lines[0])
+    assert d["impl"] == "reference" and d["unit"] == "attempts/s" and d["value"] > 0
+    assert d["steps"] == 1 and d["warmup"] == 1 and d["higher_is_better"] is True
+    assert d["cpu_baseline"]["kind"] == "oracle" and d["cpu_baseline"]["cores"] >= 1
+    assert d["cpu_baseline"]["value"] == d["value"] and d["cpu_baseline"]["sample"]
+    assert d["e2e"] == {"value": d["value"], "unit": "attempts/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}
+    assert d["config"]["L"] == 32 and d["config"]["walkers"] == 16384
