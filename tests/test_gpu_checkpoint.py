@@ -188,3 +188,32 @@ def test_device_and_batched_iterations_resume(muca_mod, tmp_path, mode):
             assert np.array_equal(m.get_weights(), w) and m.info()[2] == t
         for m in ms:
             m.close()
+
+
+def test_earlier_format_loads_with_a_fresh_schedule(muca_mod, tmp_path):
+    """A file of the earlier format (magic MUCACKP1, no iteration state after the header)
+    restores the same lattices, energies, weights, histogram and counter, with the
+    iteration state of a new instance."""
+    M = muca_mod
+    L, W = 16, 70
+    lnW = np.cumsum(np.random.default_rng(3).normal(0, 0.3, L * L + 1))
+    v2, v1 = str(tmp_path / "v2.muca"), str(tmp_path / "v1.muca")
+    with M.Muca(L, W, 5) as a:
+        a.set_weights(lnW)
+        a.iterate_until_flat(M.make_params(therm_sweeps=2, sweeps_per_iter=3, max_iterations=2))
+        a.save(v2)
+        ref = snapshot(a)
+    raw = open(v2, "rb").read()
+    head = 8 + 4 + 4 + 8 + 8 + 4 + 4 + 8 + 8          # magic .. first_walker
+    assert raw[:8] == b"MUCACKP2"
+    open(v1, "wb").write(b"MUCACKP1" + raw[8:head] + raw[head + 4 * 4 + 8:])
+    with M.Muca.load(v1) as b:
+        for x, y in zip(ref, snapshot(b)):
+            assert np.array_equal(x, y)
+        log = []
+        b.set_iteration_observer(lambda it, H, metric, nt, nu: log.append(nu))
+        b.iterate_until_flat(M.make_params(schedule=M.MUCA_SCHEDULE_PAPER, stop_rule=M.MUCA_STOP_KL,
+                                           flat_threshold=1e-4, max_iterations=1, resume=True))
+        b.set_iteration_observer(None)
+    # a fresh state: w' = 0, so the first N_updates is Eq. (7) at w = 10
+    assert log == [int(np.floor(6.0 * 10 ** 2.25 / W)) + 1]
