@@ -317,10 +317,11 @@ int muca_batch_create(const muca_t *instances, int32_t n, muca_batch_t *out)
     size_t items = 0;
     for (muca_t h : b->inst) {
         int32_t wpb = 256;
-        while (wpb > 32 && muca::full_smem_bytes(h->L, wpb, true) > limit)
+        const int stride = muca::batch_table_stride(h->L);
+        while (wpb > 32 && muca::full_smem_bytes(h->L, wpb, true, false, stride) > limit)
             wpb -= 32;
         b->item_wpb.push_back(wpb);
-        b->smem = std::max(b->smem, muca::full_smem_bytes(h->L, wpb, true));
+        b->smem = std::max(b->smem, muca::full_smem_bytes(h->L, wpb, true, false, stride));
         items += (size_t)((h->W + wpb - 1) / wpb);
     }
     b->items_capacity = items;

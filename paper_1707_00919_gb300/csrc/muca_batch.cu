@@ -38,7 +38,7 @@ __global__ void __launch_bounds__(256, 1) batch_kernel(const SweepArgs *__restri
         case 24: batch_item<24, RECORD>(a, it, smem); break;
         case 32: batch_item<32, RECORD>(a, it, smem); break;
         case 48: batch_item<48, RECORD>(a, it, smem); break;
-        case 64: batch_item<64, RECORD>(a, it, smem); break;
+        case 64: batch_item<64, RECORD, false, batch_table_stride(64)>(a, it, smem); break;
         default: break;
         }
     }

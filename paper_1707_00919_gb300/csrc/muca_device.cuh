@@ -42,7 +42,9 @@ __device__ __forceinline__ uint32_t bit_at(RowT w, int x)
 // thresholds T[e][k], word 5 the block's histogram count of e, word 6 padding (a stride
 // of 7 words spreads the rows over all 32 banks; thermalization counts go there).  The energy is carried as the byte
 // address E of its row, so a threshold is at E + 4k, the histogram word at E + 20, and
-// an accepted flip moves E by 28 (2 - k).
+// an accepted flip moves E by 28 (2 - k).  The batched kernel's L = 64 items use 6-word
+// rows instead (24 bytes, thermalization counts in the histogram word, which such
+// launches never read), which lets 256 walkers share an SM with the 4097-row table.
 //
 // Latency: the threshold an attempt needs depends on whether the previous attempt
 // flipped (through E and through k).  Both candidates are loaded two attempts ahead and
@@ -314,13 +316,18 @@ __device__ __forceinline__ void hist_add_one(uint32_t E)
     asm volatile("red.shared.add.u32 [%0+20], 1;" :: "r"(E));
 }
 
-// Thermalization launches add the same count to the row's padding word (offset 24),
-// which nothing reads.  The reduction orders the shared-memory threshold loads of later
-// attempts behind it exactly as in a recording launch; without it the compiler's
-// schedule was measured 11% slower (72 vs 64 cycles per attempt and warp at L = 32).
+// Thermalization launches add the same count to the row's padding word (offset 24; with
+// 6-word rows the histogram word, which such launches never flush), which nothing reads.
+// The reduction orders the shared-memory threshold loads of later attempts behind it
+// exactly as in a recording launch; without it the compiler's schedule was measured 11%
+// slower (72 vs 64 cycles per attempt and warp at L = 32).
+template <int STRIDE>
 __device__ __forceinline__ void pad_add_one(uint32_t E)
 {
-    asm volatile("red.shared.add.u32 [%0+24], 1;" :: "r"(E));
+    if (STRIDE == 7)
+        asm volatile("red.shared.add.u32 [%0+24], 1;" :: "r"(E));
+    else
+        asm volatile("red.shared.add.u32 [%0+20], 1;" :: "r"(E));
 }
 
 // Byte offset 4k of the count field x (k in 0..4) of a nibble word.
@@ -347,7 +354,7 @@ struct PhiloxSource {
 
 // MASKED: only the attempts x in [x_begin, x_end) happen (a launch that starts or ends
 // inside the row); the others neither flip nor count, their random words go unused.
-template <int L, bool RECORD, bool MASKED, class Src>
+template <int L, bool RECORD, bool MASKED, class Src, int STRIDE = kTableStride>
 __device__ __forceinline__ void process_row(const uint32_t (&U)[L / 8], uint32_t (&C)[L / 8], const uint32_t (&D)[L / 8],
                                             uint32_t &E, const Src &src, int x_begin = 0, int x_end = L)
 {
@@ -382,8 +389,10 @@ __device__ __forceinline__ void process_row(const uint32_t (&U)[L / 8], uint32_t
     uint32_t J0a, J1a, J0b, J1b;
     MUCA_SITE_J(0, J0a, J1a);
     MUCA_SITE_J(1, J0b, J1b);
-    uint32_t d0_cur = 56u - 7u * J0a, d1_cur = d0_cur;               // attempt x
-    uint32_t d0_next = 56u - 7u * J0b, d1_next = 56u - 7u * J1b;     // attempt x + 1
+    // row step of a flip with count k = J / 4: 4 STRIDE (2 - k) bytes
+    constexpr uint32_t kD2 = 8u * STRIDE, kDJ = STRIDE;
+    uint32_t d0_cur = kD2 - kDJ * J0a, d1_cur = d0_cur;               // attempt x
+    uint32_t d0_next = kD2 - kDJ * J0b, d1_next = kD2 - kDJ * J1b;    // attempt x + 1
     uint32_t T0n = lds_u32(E + J0a), T1n = T0n;                      // candidates of x
     uint32_t T0nn = lds_u32(E + J0b), T1nn = lds_u32(E + d0_cur + J1b);   // of x + 1
     bool prev_acc = false;
@@ -409,7 +418,7 @@ __device__ __forceinline__ void process_row(const uint32_t (&U)[L / 8], uint32_t
             if (RECORD && in_range)
                 hist_add_one(Epost);
             else
-                pad_add_one(Epost);
+                pad_add_one<STRIDE>(Epost);
             // candidates of attempt x + 2 for both outcomes of attempt x + 1
             T0n = T0nn;
             T1n = T1nn;
@@ -422,8 +431,8 @@ __device__ __forceinline__ void process_row(const uint32_t (&U)[L / 8], uint32_t
                 T1nn = lds_u32(a1);
                 d0_cur = d0_next;
                 d1_cur = d1_next;
-                d0_next = 56u - 7u * J0c;
-                d1_next = 56u - 7u * J1c;
+                d0_next = kD2 - kDJ * J0c;
+                d1_next = kD2 - kDJ * J1c;
             } else if (x + 1 < L) {
                 d0_cur = d0_next;
                 d1_cur = d1_next;
@@ -443,7 +452,7 @@ __device__ __forceinline__ void process_row(const uint32_t (&U)[L / 8], uint32_t
 // compile-time layout get it folded, the batched kernels pass it at run time.  GUARD
 // adds kTableGuard zero rows on both sides of the table, for energies that come from the
 // caller and need not match the lattices (the library's own energies always do).
-template <int L, bool RECORD, bool PARTIAL = false, bool GUARD = false>
+template <int L, bool RECORD, bool PARTIAL = false, bool GUARD = false, int STRIDE = kTableStride>
 __device__ __forceinline__ void sweep_block(const SweepArgs &a, int64_t wbase, int wpb, unsigned char *smem,
                                             const int LAYOUT)
 {
@@ -459,7 +468,7 @@ __device__ __forceinline__ void sweep_block(const SweepArgs &a, int64_t wbase, i
     const int tid = threadIdx.x;
     constexpr int G = GUARD ? kTableGuard : 0;
     constexpr int NR = NB + 2 * G;   // table rows: energies -G .. N + G
-    const SmemRows<L> rows{smem + align_up((size_t)NR * kTableStride * 4, 16), wpb, tid};
+    const SmemRows<L> rows{smem + align_up((size_t)NR * STRIDE * 4, 16), wpb, tid};
     const int lane = tid & 31;
     const bool in_item = tid < wpb;
     const int64_t w = wbase + tid;
@@ -468,14 +477,14 @@ __device__ __forceinline__ void sweep_block(const SweepArgs &a, int64_t wbase, i
     const bool warp_full = in_item && (w0 + 32 <= a.W) && (a.W % 16 == 0);
 
     if (GUARD) {
-        for (int i = tid; i < NR * kTableStride; i += nthr) {
-            const int r = i / kTableStride, k = i - r * kTableStride;
+        for (int i = tid; i < NR * STRIDE; i += nthr) {
+            const int r = i / STRIDE, k = i - r * STRIDE;
             const int e = r - G;
             sTab[i] = (k < 5 && e >= 0 && e <= N) ? a.table[e * 5 + k] : 0u;
         }
     } else {
-        for (int i = tid; i < NB * kTableStride; i += nthr) {
-            const int e = i / kTableStride, k = i - e * kTableStride;
+        for (int i = tid; i < NB * STRIDE; i += nthr) {
+            const int e = i / STRIDE, k = i - e * STRIDE;
             sTab[i] = k < 5 ? a.table[e * 5 + k] : 0u;
         }
     }
@@ -513,9 +522,9 @@ __device__ __forceinline__ void sweep_block(const SweepArgs &a, int64_t wbase, i
 
     if (active) {
         const PhiloxKeys pk = make_keys(a.seed, a.walker0 + (uint32_t)w);
-        const uint32_t tbase = (uint32_t)__cvta_generic_to_shared(sTab) + G * kTableStride * 4u;
+        const uint32_t tbase = (uint32_t)__cvta_generic_to_shared(sTab) + G * STRIDE * 4u;
         uint32_t U[NW], C[NW], D[NW];
-        uint32_t E = tbase + (uint32_t)e * (4u * kTableStride);
+        uint32_t E = tbase + (uint32_t)e * (4u * STRIDE);
         if (!PARTIAL) {
             // whole sweeps from a sweep boundary
             uint64_t blk = a.t0 >> 2;
@@ -527,7 +536,7 @@ __device__ __forceinline__ void sweep_block(const SweepArgs &a, int64_t wbase, i
 #pragma unroll 1
                 for (int y = 0; y < L; ++y) {
                     const PhiloxSource src{blk, &pk};
-                    process_row<L, RECORD, false>(U, C, D, E, src);
+                    process_row<L, RECORD, false, PhiloxSource, STRIDE>(U, C, D, E, src);
                     rows.store(y, C);
                     const int y2 = (y + 2 < L) ? y + 2 : y + 2 - L;
 #pragma unroll
@@ -554,10 +563,10 @@ __device__ __forceinline__ void sweep_block(const SweepArgs &a, int64_t wbase, i
                 const PhiloxSource src{blk, &pk};
                 int xe = L;
                 if (x0 == 0 && left >= (uint64_t)L) {
-                    process_row<L, RECORD, false>(U, C, D, E, src);
+                    process_row<L, RECORD, false, PhiloxSource, STRIDE>(U, C, D, E, src);
                 } else {
                     xe = left < (uint64_t)(L - x0) ? x0 + (int)left : L;
-                    process_row<L, RECORD, true>(U, C, D, E, src, x0, xe);
+                    process_row<L, RECORD, true, PhiloxSource, STRIDE>(U, C, D, E, src, x0, xe);
                 }
                 rows.store(y, C);
                 t += (uint64_t)(xe - x0);
@@ -575,14 +584,14 @@ __device__ __forceinline__ void sweep_block(const SweepArgs &a, int64_t wbase, i
                 blk += (uint64_t)(L / 4);
             }
         }
-        e = (int32_t)((E - tbase) / (4u * kTableStride));
-        if (E < tbase || e > N || (E - tbase) % (4u * kTableStride) != 0u)   // corrupted energy address
+        e = (int32_t)((E - tbase) / (4u * STRIDE));
+        if (E < tbase || e > N || (E - tbase) % (4u * STRIDE) != 0u)   // corrupted energy address
             atomicOr(a.err, kErrEnergyRange);
     }
     __syncthreads();
     if (RECORD)
         for (int i = tid; i < NB; i += nthr) {
-            const uint32_t v = sTab[(i + G) * kTableStride + kHistSlot];
+            const uint32_t v = sTab[(i + G) * STRIDE + kHistSlot];
             if (v)
                 atomicAdd(&a.hist[i], (unsigned long long)v);
         }
@@ -607,10 +616,10 @@ __device__ __forceinline__ void sweep_block(const SweepArgs &a, int64_t wbase, i
 }
 
 // A batched work item: the whole-sweep body of the item's instance.
-template <int L, bool RECORD, bool GUARD = false>
+template <int L, bool RECORD, bool GUARD = false, int STRIDE = kTableStride>
 __device__ __forceinline__ void batch_item(const SweepArgs &a, const BatchItem &it, unsigned char *smem)
 {
-    sweep_block<L, RECORD, false, GUARD>(a, it.wbase, it.wpb, smem, a.layout);
+    sweep_block<L, RECORD, false, GUARD, STRIDE>(a, it.wbase, it.wpb, smem, a.layout);
 }
 
 }  // namespace

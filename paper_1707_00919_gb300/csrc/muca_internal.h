@@ -18,6 +18,9 @@ constexpr int kHistSlot = 5;
 // within two rows of the current energy, so they stay inside the table even for
 // energies that do not match the lattices.
 constexpr int kTableGuard = 2;
+// Table row stride of the batched kernel: 6 words at L = 64 (the histogram word doubles
+// as the thermalization padding), so that 256 walkers fit next to the 4097-row table.
+__host__ __device__ constexpr int batch_table_stride(int L) { return L == 64 ? 6 : kTableStride; }
 
 // Device error word bits.
 constexpr uint32_t kErrEnergyRange = 1u;   // a walker's energy index was off the grid
@@ -75,7 +78,7 @@ constexpr int kBatchThreads = 256;   // threads per block of the batched kernel
 size_t sweep_smem_bytes(int L, int walkers_per_block, bool record);
 
 // Shared memory bytes of the whole-sweep kernel (eight thresholds per energy).
-size_t full_smem_bytes(int L, int walkers_per_block, bool record, bool guard = false);
+size_t full_smem_bytes(int L, int walkers_per_block, bool record, bool guard = false, int stride = kTableStride);
 
 // Largest dynamic shared memory a block may use on this device (bytes).
 size_t sweep_smem_limit();

@@ -321,12 +321,12 @@ cudaError_t launch_sweep_row(const SweepArgs &a, int wpb, bool record, cudaStrea
 
 }  // namespace
 
-size_t full_smem_bytes(int L, int wpb, bool record, bool guard)
+size_t full_smem_bytes(int L, int wpb, bool record, bool guard, int stride)
 {
     (void)record;
     const size_t rows = (size_t)L * L + 1 + (guard ? 2 * kTableGuard : 0);
     const size_t per_walker = L <= 32 ? (size_t)L * (L / 8) * 4 : (size_t)L * 8;
-    return align_up(rows * kTableStride * 4, 16) + per_walker * (size_t)wpb;
+    return align_up(rows * (size_t)stride * 4, 16) + per_walker * (size_t)wpb;
 }
 
 size_t sweep_smem_bytes(int L, int wpb, bool record)
