@@ -381,7 +381,8 @@ def run_native(args):
     # measured issue rates of the instruction classes the sweep uses (context for the peak)
     probe = {name: M.muca_measure_issue_rate(kind) / 1e12
              for name, kind in (("xor3_alu", M.MUCA_PROBE_XOR), ("imad", M.MUCA_PROBE_MAD),
-                                ("xor3_imad_alternating", M.MUCA_PROBE_MIXED))}
+                                ("xor3_imad_alternating", M.MUCA_PROBE_MIXED),
+                                ("xor3_imad_alternating_one_warp_per_smsp", M.MUCA_PROBE_MIXED_ONE_WARP))}
     philox_words = M.muca_measure_issue_rate(M.MUCA_PROBE_PHILOX)
     result = {
         "metric": "spin-flip attempts/s (and time-to-flat H) at L=32, 16384 walkers; % of integer-issue roofline",

@@ -201,14 +201,17 @@ int muca_load(const char *path, muca_t *out);
  * of independent work, for the integer roofline of the sweep kernels.  kind:
  * MUCA_PROBE_XOR (three-input XOR: the integer ALU pipe), MUCA_PROBE_MAD (32-bit
  * multiply-add), MUCA_PROBE_MIXED (the two alternating), MUCA_PROBE_PHILOX
- * (Philox4x32-10 words, Sec. 2.3's generator).  *per_second receives thread
- * instructions per second (words per second for MUCA_PROBE_PHILOX).  Runs for about
- * 0.1 s; allocates 4 KiB of device memory.  Errors: MUCA_EINVAL (unknown kind, NULL),
- * MUCA_ECUDA. */
+ * (Philox4x32-10 words, Sec. 2.3's generator), MUCA_PROBE_MIXED_ONE_WARP (the
+ * alternating mix with one warp per sub-partition, eight independent chains per thread:
+ * what a single warp can issue, the situation of the sweep kernels at 16384 walkers).
+ * *per_second receives thread instructions per second (words per second for
+ * MUCA_PROBE_PHILOX).  Runs for about 0.1 s; allocates 4 KiB of device memory.
+ * Errors: MUCA_EINVAL (unknown kind, NULL), MUCA_ECUDA. */
 #define MUCA_PROBE_XOR 0
 #define MUCA_PROBE_MAD 1
 #define MUCA_PROBE_MIXED 2
 #define MUCA_PROBE_PHILOX 3
+#define MUCA_PROBE_MIXED_ONE_WARP 4
 int muca_measure_issue_rate(int32_t kind, double *per_second);
 
 /* Site order of later updates (sweeps, attempts, iterations, production):

@@ -32,6 +32,7 @@ MUCA_PROBE_XOR = 0
 MUCA_PROBE_MAD = 1
 MUCA_PROBE_MIXED = 2
 MUCA_PROBE_PHILOX = 3
+MUCA_PROBE_MIXED_ONE_WARP = 4
 
 MUCA_STOP_MIN_MEAN = 0
 MUCA_STOP_KL = 1

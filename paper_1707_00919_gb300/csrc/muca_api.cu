@@ -494,7 +494,7 @@ int muca_measure_issue_rate(int32_t kind, double *per_second)
 {
     if (!per_second)
         return fail(MUCA_EINVAL, "NULL argument");
-    if (kind < MUCA_PROBE_XOR || kind > MUCA_PROBE_PHILOX)
+    if (kind < MUCA_PROBE_XOR || kind > MUCA_PROBE_MIXED_ONE_WARP)
         return fail(MUCA_EINVAL, "unknown probe kind %d", kind);
     MUCA_CUDA(muca::measure_issue_rate(kind, per_second), "issue-rate probe");
     return MUCA_OK;

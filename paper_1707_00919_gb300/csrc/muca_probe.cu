@@ -1,8 +1,9 @@
 // muca_probe.cu - integer issue-rate measurement for the roofline of the sweep kernels:
 // independent streams of one instruction class on every SM sub-partition (16 warps
 // each), timed with CUDA events.  Kinds: three-input XOR (the integer ALU pipe),
-// 32-bit multiply-add (the multiply pipe), the two alternating, and Philox4x32-10
-// words (the generator of the sweep kernels).
+// 32-bit multiply-add (the multiply pipe), the two alternating, Philox4x32-10 words
+// (the generator of the sweep kernels), and the alternating mix with a single warp per
+// sub-partition.
 #include <cstdint>
 
 #include <cuda_runtime.h>
@@ -59,19 +60,20 @@ __global__ void __launch_bounds__(kProbeThreads) probe_kernel(uint32_t iters, ui
 }
 
 template <int KIND>
-cudaError_t run_probe(int blocks, uint32_t iters, uint32_t *sink, cudaStream_t s)
+cudaError_t run_probe(int blocks, int threads, uint32_t iters, uint32_t *sink, cudaStream_t s)
 {
-    probe_kernel<KIND><<<blocks, kProbeThreads, 0, s>>>(iters, 0x2545F491u, sink);
+    probe_kernel<KIND><<<blocks, threads, 0, s>>>(iters, 0x2545F491u, sink);
     return cudaGetLastError();
 }
 
-cudaError_t launch_probe(int kind, int blocks, uint32_t iters, uint32_t *sink, cudaStream_t s)
+cudaError_t launch_probe(int kind, int blocks, int threads, uint32_t iters, uint32_t *sink, cudaStream_t s)
 {
     switch (kind) {
-    case MUCA_PROBE_XOR: return run_probe<MUCA_PROBE_XOR>(blocks, iters, sink, s);
-    case MUCA_PROBE_MAD: return run_probe<MUCA_PROBE_MAD>(blocks, iters, sink, s);
-    case MUCA_PROBE_MIXED: return run_probe<MUCA_PROBE_MIXED>(blocks, iters, sink, s);
-    default: return run_probe<MUCA_PROBE_PHILOX>(blocks, iters, sink, s);
+    case MUCA_PROBE_XOR: return run_probe<MUCA_PROBE_XOR>(blocks, threads, iters, sink, s);
+    case MUCA_PROBE_MAD: return run_probe<MUCA_PROBE_MAD>(blocks, threads, iters, sink, s);
+    case MUCA_PROBE_MIXED:
+    case MUCA_PROBE_MIXED_ONE_WARP: return run_probe<MUCA_PROBE_MIXED>(blocks, threads, iters, sink, s);
+    default: return run_probe<MUCA_PROBE_PHILOX>(blocks, threads, iters, sink, s);
     }
 }
 
@@ -85,7 +87,10 @@ cudaError_t measure_issue_rate(int kind, double *per_second)
         err = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
     if (err != cudaSuccess)
         return err;
-    const int blocks = sms * 8;   // 2048 threads per SM: 16 warps per sub-partition
+    // 2048 threads per SM (16 warps per sub-partition), or 128 (one warp per sub-partition)
+    const bool one_warp = kind == MUCA_PROBE_MIXED_ONE_WARP;
+    const int threads = one_warp ? 128 : kProbeThreads;
+    const int blocks = one_warp ? sms : sms * 8;
     uint32_t *sink = nullptr;
     cudaStream_t s = nullptr;
     cudaEvent_t a = nullptr, b = nullptr;
@@ -100,11 +105,11 @@ cudaError_t measure_issue_rate(int kind, double *per_second)
     uint32_t iters = 1024;
     float ms = 0.0f;
     for (int pass = 0; err == cudaSuccess && pass < 12; ++pass) {
-        err = launch_probe(kind, blocks, iters / 4, sink, s);   // warm-up
+        err = launch_probe(kind, blocks, threads, iters / 4, sink, s);   // warm-up
         if (err == cudaSuccess)
             err = cudaEventRecord(a, s);
         if (err == cudaSuccess)
-            err = launch_probe(kind, blocks, iters, sink, s);
+            err = launch_probe(kind, blocks, threads, iters, sink, s);
         if (err == cudaSuccess)
             err = cudaEventRecord(b, s);
         if (err == cudaSuccess)
@@ -116,10 +121,10 @@ cudaError_t measure_issue_rate(int kind, double *per_second)
         iters *= 4;
     }
     if (err == cudaSuccess) {
-        const double threads = (double)blocks * kProbeThreads;
+        const double all_threads = (double)blocks * threads;
         // per thread and iteration: kChains instructions, or one Philox call (4 words)
         const double units = kind == MUCA_PROBE_PHILOX ? 4.0 : (double)kChains;
-        *per_second = threads * (double)iters * units / ((double)ms * 1e-3);
+        *per_second = all_threads * (double)iters * units / ((double)ms * 1e-3);
     }
     if (a)
         cudaEventDestroy(a);

@@ -16,7 +16,8 @@ import numpy as np
 from . import _lib as C
 from ._lib import (MUCA_LAYOUT_AUTO, MUCA_LAYOUT_INT8, MUCA_LAYOUT_PACKED, MUCA_OK,  # noqa: F401
                    MUCA_ORDER_RANDOM, MUCA_ORDER_TYPEWRITER, MUCA_PROBE_MAD, MUCA_PROBE_MIXED,
-                   MUCA_PROBE_PHILOX, MUCA_PROBE_XOR, MUCA_SCHEDULE_PAPER, MUCA_WALKERS_OPTIMAL,
+                   MUCA_PROBE_MIXED_ONE_WARP, MUCA_PROBE_PHILOX, MUCA_PROBE_XOR, MUCA_SCHEDULE_PAPER,
+                   MUCA_WALKERS_OPTIMAL,
                    MUCA_WPB_TUNE,
                    MUCA_SCHEDULE_SWEEPS, MUCA_STOP_CHEBYSHEV, MUCA_STOP_KL, MUCA_STOP_MIN_MEAN,
                    muca_options, muca_params, muca_stats)

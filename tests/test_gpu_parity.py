@@ -278,6 +278,8 @@ def test_issue_rate_probe(muca_mod):
         assert 0.05 * ceiling < r < 1.05 * ceiling
     words = M.muca_measure_issue_rate(M.MUCA_PROBE_PHILOX)
     assert 1e11 < words < ceiling
+    one = M.muca_measure_issue_rate(M.MUCA_PROBE_MIXED_ONE_WARP)
+    assert 0.02 * ceiling < one < 1.05 * ceiling
     with pytest.raises(M.MucaError):
         M.muca_measure_issue_rate(9)
 
