@@ -202,7 +202,7 @@ int muca_load(const char *path, muca_t *out);
  * MUCA_PROBE_XOR (three-input XOR: the integer ALU pipe), MUCA_PROBE_MAD (32-bit
  * multiply-add), MUCA_PROBE_MIXED (the two alternating), MUCA_PROBE_PHILOX
  * (Philox4x32-10 words, Sec. 2.3's generator), MUCA_PROBE_MIXED_ONE_WARP (the
- * alternating mix with one warp per sub-partition, eight independent chains per thread:
+ * alternating mix with one warp per sub-partition, sixteen independent chains per thread:
  * what a single warp can issue, the situation of the sweep kernels at 16384 walkers).
  * *per_second receives thread instructions per second (words per second for
  * MUCA_PROBE_PHILOX).  Runs for about 0.1 s; allocates 4 KiB of device memory.

@@ -15,7 +15,7 @@ namespace muca {
 namespace {
 
 constexpr int kProbeThreads = 256;
-constexpr int kChains = 8;
+constexpr int kChains = 16;   // independent chains per thread: enough to fill one warp's issue slots
 
 template <int KIND>
 __global__ void __launch_bounds__(kProbeThreads) probe_kernel(uint32_t iters, uint32_t seed, uint32_t *sink)
