@@ -44,6 +44,10 @@ MAX_ITERATIONS = 2 * 10**4 * L_SIDE * L_SIDE // (WALKERS * SWEEPS_PER_ITER)   # 
 # load, compare, conditional flip, energy update, run-length histogram record, about
 # 15.5).  Fixed by the method, not measured from the code.
 OPS_PER_ATTEMPT = 35.0
+# Warp instructions the recorded whole-sweep kernel issues per attempt and warp (ncu
+# count, profiles/sweep_full_kernel_L32_W16384_int8.md): converts an instruction issue
+# rate into this roofline's algorithmic operations.
+INSTR_PER_ATTEMPT = 34.0
 WORKLOAD = (f"muca2d_ising_L{L_SIDE}_W{WALKERS}_int8_therm{THERM_SWEEPS}_rec{SWEEPS_PER_ITER}")
 
 
@@ -384,6 +388,12 @@ def run_native(args):
                                 ("xor3_imad_alternating", M.MUCA_PROBE_MIXED),
                                 ("xor3_imad_alternating_one_warp_per_smsp", M.MUCA_PROBE_MIXED_ONE_WARP))}
     philox_words = M.muca_measure_issue_rate(M.MUCA_PROBE_PHILOX)
+    # what one warp per sub-partition can issue, on the sub-partitions this walker count
+    # occupies (one warp per 32 walkers), as a fraction of the peak in this roofline's units
+    smsps = sm_count * 4
+    busy = min(WALKERS // 32, smsps) / smsps
+    one_warp_frac = (probe["xor3_imad_alternating_one_warp_per_smsp"] * busy * OPS_PER_ATTEMPT / INSTR_PER_ATTEMPT
+                     / peak_tops)
     result = {
         "metric": "spin-flip attempts/s (and time-to-flat H) at L=32, 16384 walkers; % of integer-issue roofline",
         "value": value,
@@ -415,6 +425,7 @@ def run_native(args):
                      "ops_per_attempt": OPS_PER_ATTEMPT,
                      "peak_basis": f"{sm_count} SMs x 4 issue slots x 32 lanes x {sm_max_mhz:.0f} MHz",
                      "measured_issue_tops": {k: round(v, 3) for k, v in probe.items()},
+                     "single_warp_issue_frac": one_warp_frac,
                      "measured_philox_words_per_s": philox_words,
                      # lattice traffic of the same launch against HBM (not the bound)
                      "hbm": {"algorithmic_bytes": lattice_bytes, "algorithmic_gbs": lattice_bytes / rec_launch_s / 1e9,
