@@ -542,11 +542,13 @@ static int orc_is_flat(int32_t rule, double metric, double thr)
  * lattices, energies, weights and attempt counter.  On return lnW holds the weights
  * of the last iteration run (unchanged by the final histogram when it was flat), and
  * t_inout the advanced attempt counter.  lnW_history[n*(N+1) + e] (optional) receives
- * the weights used in iteration n, metric_history[n] (optional) its stop metric.
+ * the weights used in iteration n, metric_history[n] (optional) its stop metric, and
+ * sched_history[4n .. 4n+3] (optional) its thermalization and update attempts per
+ * walker and the lowest and highest energy index its histogram visited (-1 if none).
  */
-int32_t orc_iterate(int32_t L, int64_t nw, uint64_t seed, int8_t *spins, int32_t *e, double *lnW,
-                    uint64_t *t_inout, const orc_params *p, double *lnW_history,
-                    double *metric_history, orc_result *res)
+int32_t orc_iterate_traced(int32_t L, int64_t nw, uint64_t seed, int8_t *spins, int32_t *e, double *lnW,
+                           uint64_t *t_inout, const orc_params *p, double *lnW_history,
+                           double *metric_history, int64_t *sched_history, orc_result *res)
 {
     const int N = L * L;
     uint64_t *H = (uint64_t *)calloc((size_t)N + 1, sizeof(uint64_t));
@@ -595,6 +597,19 @@ int32_t orc_iterate(int32_t L, int64_t nw, uint64_t seed, int8_t *spins, int32_t
         metric = orc_stop_metric(L, H, p->stop_rule, q);
         if (metric_history)
             metric_history[n] = metric;
+        if (sched_history) {
+            int64_t *rec = sched_history + 4 * (size_t)n;
+            rec[0] = (int64_t)n_therm;
+            rec[1] = (int64_t)n_upd;
+            rec[2] = -1;
+            rec[3] = -1;
+            for (int ei = 0; ei <= N; ++ei)
+                if (H[ei] > 0u) {
+                    if (rec[2] < 0)
+                        rec[2] = ei;
+                    rec[3] = ei;
+                }
+        }
         ++n;
         if (orc_is_flat(p->stop_rule, metric, p->flat_threshold)) {
             converged = 1;
@@ -623,6 +638,13 @@ int32_t orc_iterate(int32_t L, int64_t nw, uint64_t seed, int8_t *spins, int32_t
     free(H);
     free(T);
     return 0;
+}
+
+int32_t orc_iterate(int32_t L, int64_t nw, uint64_t seed, int8_t *spins, int32_t *e, double *lnW,
+                    uint64_t *t_inout, const orc_params *p, double *lnW_history,
+                    double *metric_history, orc_result *res)
+{
+    return orc_iterate_traced(L, nw, seed, spins, e, lnW, t_inout, p, lnW_history, metric_history, NULL, res);
 }
 
 /* ---------------------------------------------------------------------------------

@@ -125,6 +125,8 @@ def _bind(path: str):
         "orc_chebyshev": (dbl, [i32, P(u64)]),
         "orc_iterate": (i32, [i32, i64, u64, P(i8), P(i32), P(dbl), P(u64), P(Params),
                               P(dbl), P(dbl), P(Result)]),
+        "orc_iterate_traced": (i32, [i32, i64, u64, P(i8), P(i32), P(dbl), P(u64), P(Params),
+                                     P(dbl), P(dbl), P(i64), P(Result)]),
         "orc_ln_dos": (None, [i32, P(dbl), P(u64), P(dbl)]),
         "orc_production": (i32, [i32, i64, u64, P(i8), P(i32), P(dbl), P(u64), u64, u64,
                                  P(u64), P(dbl), i32]),
@@ -267,6 +269,23 @@ def iterate(L: int, seed: int, spins: np.ndarray, e: np.ndarray, lnW: np.ndarray
         hist = hist[: res.iterations]
         mh = mh[: res.iterations]
     return res, int(tt.value), hist, mh
+
+
+def iterate_schedule(L: int, seed: int, spins: np.ndarray, e: np.ndarray, lnW: np.ndarray, t: int,
+                     params: Params):
+    """Weight iteration as `iterate`, returning (result, t, schedule) with schedule[n] =
+    (thermalization attempts, update attempts, lowest and highest visited energy index)
+    of iteration n."""
+    nw = spins.shape[0]
+    tt = ctypes.c_uint64(t)
+    res = Result()
+    sched = np.zeros((params.max_iterations, 4), dtype=np.int64)
+    rc = lib().orc_iterate_traced(L, nw, seed, _ptr(spins, ctypes.c_int8), _ptr(e, ctypes.c_int32),
+                                  _ptr(lnW, ctypes.c_double), ctypes.byref(tt), ctypes.byref(params),
+                                  None, None, _ptr(sched, ctypes.c_int64), ctypes.byref(res))
+    if rc != 0:
+        raise MemoryError("orc_iterate_traced failed")
+    return res, int(tt.value), sched[: res.iterations]
 
 
 def ln_dos(L: int, lnW: np.ndarray, H: np.ndarray) -> np.ndarray:

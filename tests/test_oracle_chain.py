@@ -2,6 +2,7 @@
 the mathematics fix: deterministic limits of the acceptance rule, detailed balance
 against the exact density of states, flat histograms under perfect weights, and the
 density of states recovered by iteration plus production."""
+import ctypes
 import math
 
 import numpy as np
@@ -295,3 +296,111 @@ def test_paper_schedule_first_iteration_counts(orc):
     p = orc.make_params(schedule=1, stop_rule=1, flat_threshold=1e-4, max_iterations=1)
     res, t, _, _ = orc.iterate(L, 2, s, e, lnW, 0, p)
     assert res.iterations == 1 and t == 300 + 17 and res.attempts == 317
+
+
+def _kl_support(orc, L, prev, visited):
+    N = L * L
+    H = np.zeros(N + 1, dtype=np.uint64)
+    H[list(visited)] = 3
+    return int(orc.lib().orc_kl_support(L, prev[0], prev[1], H.ctypes.data_as(ctypes.POINTER(ctypes.c_uint64))))
+
+
+def test_kl_support_hand_made(orc):
+    """Reference support of the Eq. (6) measure (reading 8): the accessible energies in
+    the union of the previous iteration's range and the tested histogram's range, at
+    least 10.  Expected counts by hand; at L = 4 the inaccessible indices are 1 and 15,
+    at L = 8 they are 1 and 63."""
+    cases = [
+        # L, previous range, visited energies, expected
+        (4, (-1, -1), range(3, 10), 10),        # [3, 9]: 7 accessible, floored at 10
+        (4, (-1, -1), [0, 16], 15),             # [0, 16]: 17 points less e = 1 and 15
+        (4, (0, 14), [4, 8], 14),               # previous range wider: [0, 14] less e = 1
+        (4, (5, 9), [2, 12, 16], 14),           # visits beyond both ends: [2, 16] less e = 15
+        (4, (7, 8), [7], 10),                   # [7, 8]: 2 accessible, floored at 10
+        (4, (1, 15), [8], 13),                  # [1, 15]: 15 points less e = 1 and 15
+        (8, (10, 40), [5, 50], 46),             # [5, 50], all accessible
+        (8, (-1, -1), [63], 10),                # e = 63 alone is inaccessible: 0, floored
+        (8, (0, 64), [30], 63),                 # whole grid: N - 1 accessible energies
+    ]
+    for L, prev, vis, want in cases:
+        assert _kl_support(orc, L, prev, vis) == want, (L, prev, list(vis))
+
+
+def test_kl_measure_nonnegative_and_zero_when_flat(orc):
+    """With the reference support, d_k >= 0 for any histogram (Gibbs' inequality: Q is
+    uniform over a set that contains P's support) and d_k = 0 exactly when H is flat
+    over that set."""
+    rng = np.random.default_rng(12)
+    L = 8
+    N = L * L
+    acc = np.array([orc.lib().orc_accessible(L, e) for e in range(N + 1)], dtype=bool)
+    for _ in range(200):
+        lo, hi = sorted(rng.integers(0, N + 1, size=2))
+        H = np.zeros(N + 1, dtype=np.uint64)
+        H[lo:hi + 1] = rng.integers(0, 50, size=hi - lo + 1)
+        H[~acc] = 0
+        if H.sum() == 0:
+            continue
+        prev = (-1, -1) if rng.random() < 0.3 else tuple(sorted(rng.integers(0, N + 1, size=2)))
+        q = orc.lib().orc_kl_support(L, int(prev[0]), int(prev[1]),
+                                     H.ctypes.data_as(ctypes.POINTER(ctypes.c_uint64)))
+        assert orc.kullback_leibler(L, H, q) >= -1e-15
+    # flat over the accessible energies of the union [3, 40] of [3, 20] and [10, 40]
+    H = np.zeros(N + 1, dtype=np.uint64)
+    H[10:41] = 7
+    q = orc.lib().orc_kl_support(L, 3, 20, H.ctypes.data_as(ctypes.POINTER(ctypes.c_uint64)))
+    assert q == 38
+    Hf = np.zeros(N + 1, dtype=np.uint64)
+    Hf[3:41] = 7
+    assert orc.kullback_leibler(L, Hf, q) == pytest.approx(0.0, abs=1e-15)
+    # H covering only part of it: P = 1/31 on 31 energies, Q = 1/38, d_k = ln(38/31)
+    assert orc.kullback_leibler(L, H, q) == pytest.approx(math.log(38 / 31), rel=1e-12)
+
+
+def test_paper_schedule_trace(orc):
+    """Eq. (7) schedule of Sec. 3 (f_therm = 30, z = 2.25, factor 6, growth 1.1) over the
+    first seven iterations of L = 4, W = 4, seed 1, derived by hand from the visited
+    ranges the run records (w = max(w', 10), w' = e_max - e_min + 1 of the previous
+    iteration, N_therm = 30 w, N_updates = floor(6 w^2.25 / W) + 1 while the iteration
+    starts below the full width N + 1 = 17, that first full-width iteration included;
+    floor(1.1 N_prev) + 1 after it):
+      it 0: no range yet, w = 10: 300, floor(6 * 177.828 / 4) + 1 = 267; visits [5, 11]
+      it 1: w' = 7, w = 10: 300, 267; visits [2, 14]
+      it 2: w = 13: 390, floor(6 * 320.90 / 4) + 1 = 482; visits [0, 16]
+      it 3: w = 17 = N + 1: 510, floor(6 * 586.83 / 4) + 1 = 881 (still Eq. 7)
+      it 4: 510, floor(1.1 * 881) + 1 = 970
+      it 5: 510, floor(1.1 * 970) + 1 = 1068
+      it 6: 510, floor(1.1 * 1068) + 1 = 1175"""
+    L, W, seed = 4, 4, 1
+    N = L * L
+    s, e = orc.init(L, seed, W)
+    lnW = np.zeros(N + 1)
+    p = orc.make_params(schedule=1, stop_rule=1, flat_threshold=1e-4, max_iterations=7)
+    res, t, sched = orc.iterate_schedule(L, seed, s, e, lnW, 0, p)
+    want = [(300, 267, 5, 11), (300, 267, 2, 14), (390, 482, 0, 16), (510, 881, 0, 16),
+            (510, 970, 0, 16), (510, 1068, 0, 16), (510, 1175, 0, 16)]
+    assert res.iterations == 7
+    assert [tuple(int(v) for v in r) for r in sched] == want
+    assert t == sum(a + b for a, b, _, _ in want) and res.attempts == t
+
+
+def test_paper_schedule_trace_recurrence(orc):
+    """The same rules over longer runs of other walker counts: each iteration's counts
+    follow from the previous iteration's recorded range and counts."""
+    for L, W, seed in [(4, 2, 5), (4, 16, 3), (8, 64, 2)]:
+        N = L * L
+        s, e = orc.init(L, seed, W)
+        lnW = np.zeros(N + 1)
+        p = orc.make_params(schedule=1, stop_rule=1, flat_threshold=1e-4, max_iterations=14)
+        res, t, sched = orc.iterate_schedule(L, seed, s, e, lnW, 0, p)
+        full, prev_w, prev_upd = False, 0, 0
+        for therm, upd, lo, hi in sched:
+            w = max(prev_w, 10)
+            assert therm == 30 * w
+            if full:
+                assert upd == math.floor(1.1 * prev_upd) + 1
+            else:
+                assert upd == math.floor(6.0 * w ** 2.25 / W) + 1
+                full = prev_w == N + 1
+            prev_w, prev_upd = hi - lo + 1, upd
+        assert full, (L, W)

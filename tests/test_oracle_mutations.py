@@ -1,8 +1,9 @@
 """The pins catch plausible mistakes in the oracle: each case plants one mistake in a copy
 of the oracle's C source (a flipped sign, a wrong energy step, a dropped neighbour, the
 histogram recorded before the decision, the recursion's sign, the Kullback-Leibler
-reference, a Philox constant, the exp series, the tag of the random-order site stream,
-the energy step of a random-order flip), builds it, and runs the existing pin tests
+reference and its support, a Philox constant, the exp series, the tag of the random-order
+site stream, the energy step of a random-order flip, the Eq. (7) schedule's width and its
+switch to the growth rule), builds it, and runs the existing pin tests
 against it; at least one must fail.  A planted mistake can drive an index off the grid,
 so the pins of each copy run in a child process: a failed assertion or a crash both
 count as caught.  The unmodified copy passes the same pins through the same path."""
@@ -27,6 +28,8 @@ PINS = {
     "math": ("test_oracle_math", ["test_exp_against_libm", "test_exp_special_values"]),
     "random": ("test_oracle_random_order", ["test_site_definition", "test_all_accept_limit", "test_quench_limit",
                                             "test_splits_compose_and_energy_tracked"]),
+    "schedule": ("test_oracle_chain", ["test_kl_support_hand_made", "test_kl_measure_nonnegative_and_zero_when_flat",
+                                       "test_paper_schedule_first_iteration_counts", "test_paper_schedule_trace"]),
 }
 
 _RANDOM_TAIL = "            }\n            if (record)\n                H[ew] += 1u;\n        }\n        e[w] = ew;\n    }\n}\n\n/* Updates in the order"
@@ -50,6 +53,13 @@ MUTATIONS = [
      "orc_random_word(seed, ORC_SHARED_STREAM, ORC_TAG_METROPOLIS, t);", "random"),
     ("energy step of a random-order flip", "                ew += 2 - k;\n" + _RANDOM_TAIL,
      "                ew += k - 2;\n" + _RANDOM_TAIL, "random"),
+    ("Kullback-Leibler support from the previous range only",
+     "            if (lo < 0 || e < lo)\n                lo = e;\n            if (hi < 0 || e > hi)\n                hi = e;",
+     "            ;", "schedule"),
+    ("growth rule one iteration early", "            if (full) {", "            if (full || prev_width == N + 1) {",
+     "schedule"),
+    ("schedule width as the accessible count", "        prev_width = orc_width(L, H);",
+     "        prev_width = orc_accessible_in_range(L, H);", "schedule"),
 ]
 
 
