@@ -466,12 +466,13 @@ int muca_server_totals(muca_server_t s, uint64_t *walker_attempts, double *secon
  * a plugin whose host forbids allocation after initialisation, or a loop that cannot
  * afford the device-wide synchronisation a cudaMalloc/cudaFree may cause.  Such a caller
  * passes its own device buffers; the call allocates nothing (no cudaMalloc, cudaFree or
- * allocating library routine).  The kernel's scratch (instance descriptors, work-list
- * bookkeeping and the work counter, MUCA_NOALLOC_SCRATCH_BYTES in total) is a fixed array
- * in device memory that every GPU loading this library keeps until the process exits.
+ * allocating library routine).  The kernel's one piece of scratch, its work counter, sits
+ * in a fixed array of MUCA_NOALLOC_SCRATCH_BYTES in device memory that every GPU loading
+ * this library keeps until the process exits; the instance descriptors travel in the
+ * kernel's launch parameters.
  * -------------------------------------------------------------------------------- */
 #define MUCA_NOALLOC_MAX_INSTANCES 64
-#define MUCA_NOALLOC_SCRATCH_BYTES 8192
+#define MUCA_NOALLOC_SCRATCH_BYTES 256
 
 /* One instance's state in caller-owned device memory, in the layouts of this header:
  * lattice in `layout`, energy indices int32[n_walkers], thresholds uint32[(L*L+1)*5]
@@ -500,14 +501,16 @@ typedef struct {
  * same state.  The caller advances its t0 by n_sweeps * L * L afterwards.
  *  - The first call on a device looks up the scratch array's device address (once per
  *    device, with that device current); make that first call before any stream capture.
- *  - The instance table is copied from the caller's host array, so the array may be
- *    reused as soon as the call returns.
- *  - All calls share the one scratch array, which keeps the last call's contents: calls
- *    that overlap on the GPU (other streams, other host threads) race and must not be
- *    issued.
+ *  - The instance array is read during the call (its descriptors become the kernel's
+ *    launch parameters), so it may be reused as soon as the call returns.
+ *  - All calls share the one scratch array, which keeps the last call's contents (each
+ *    call zeroes the work counter on cuda_stream before its launch): calls that overlap
+ *    on the GPU (other streams, other host threads) race and must not be issued.
  * Errors: MUCA_EINVAL (NULL, more than MUCA_NOALLOC_MAX_INSTANCES instances, L outside
  * the list, t0 off a sweep boundary, a recorded launch longer than 0xFFFFFFFF / 256
- * attempts per walker), MUCA_ECUDA. */
+ * attempts per walker, more than 2^31 - 1 work items of up to 256 walkers, two instances
+ * whose lattice or energy buffers overlap, the same instance given twice included),
+ * MUCA_ECUDA. */
 int muca_batch_sweep_noalloc(const muca_raw_instance *instances, int32_t n, uint64_t n_sweeps, int record,
                              void *cuda_stream);
 

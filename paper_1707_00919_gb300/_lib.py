@@ -85,7 +85,7 @@ class muca_raw_instance(ctypes.Structure):
 
 
 MUCA_NOALLOC_MAX_INSTANCES = 64
-MUCA_NOALLOC_SCRATCH_BYTES = 8192
+MUCA_NOALLOC_SCRATCH_BYTES = 256
 
 ALLOC_FN = ctypes.CFUNCTYPE(ctypes.c_void_p, ctypes.c_size_t, ctypes.c_void_p)
 RELEASE_FN = ctypes.CFUNCTYPE(None, ctypes.c_void_p, ctypes.c_void_p)

@@ -517,6 +517,13 @@ int muca_batch_iterate(muca_batch_t b, const muca_params *p_in, muca_stats *stat
     return fail(MUCA_ENOTCONVERGED, "not every instance became flat");
 }
 
+// Whether the byte ranges [a, a + na) and [b, b + nb) intersect.
+static bool overlaps(const void *a, size_t na, const void *b, size_t nb)
+{
+    const uintptr_t pa = reinterpret_cast<uintptr_t>(a), pb = reinterpret_cast<uintptr_t>(b);
+    return pa < pb + nb && pb < pa + na;
+}
+
 int muca_batch_sweep_noalloc(const muca_raw_instance *instances, int32_t n, uint64_t n_sweeps, int record,
                              void *cuda_stream)
 {
@@ -529,6 +536,9 @@ int muca_batch_sweep_noalloc(const muca_raw_instance *instances, int32_t n, uint
     const size_t limit = muca::sweep_smem_limit() - 1024;
     muca::SweepArgs descs[MUCA_NOALLOC_MAX_INSTANCES];
     int32_t wpbs[MUCA_NOALLOC_MAX_INSTANCES];
+    int32_t prefix[MUCA_NOALLOC_MAX_INSTANCES + 1];
+    prefix[0] = 0;
+    int64_t items = 0;
     size_t smem = 0;
     for (int32_t i = 0; i < n; ++i) {
         const muca_raw_instance &r = instances[i];
@@ -563,8 +573,24 @@ int muca_batch_sweep_noalloc(const muca_raw_instance *instances, int32_t n, uint
         d.table = r.table;
         d.hist = r.hist;
         d.err = r.err;
+        // work items before instance i + 1, summed in 64 bits
+        items += (r.n_walkers + wpb - 1) / wpb;
+        if (items > INT32_MAX)
+            return fail(MUCA_EINVAL, "more than %d work items of up to 256 walkers in one call", INT32_MAX);
+        prefix[i + 1] = (int32_t)items;
     }
-    MUCA_CUDA(muca::launch_batch_noalloc(descs, wpbs, n, smem, record != 0, static_cast<cudaStream_t>(cuda_stream)),
+    // every instance updates its lattices and energies in place: no two may share them
+    for (int32_t i = 0; i < n; ++i)
+        for (int32_t j = i + 1; j < n; ++j) {
+            const muca_raw_instance &a = instances[i], &b = instances[j];
+            if (overlaps(a.lattice, muca::lattice_bytes(a.L, a.layout, a.n_walkers), b.lattice,
+                         muca::lattice_bytes(b.L, b.layout, b.n_walkers)) ||
+                overlaps(a.energy, sizeof(int32_t) * (size_t)a.n_walkers, b.energy,
+                         sizeof(int32_t) * (size_t)b.n_walkers))
+                return fail(MUCA_EINVAL, "instances %d and %d share lattice or energy memory", i, j);
+        }
+    MUCA_CUDA(muca::launch_batch_noalloc(descs, wpbs, prefix, n, smem, record != 0,
+                                         static_cast<cudaStream_t>(cuda_stream)),
               "allocation-free batched sweep");
     return MUCA_OK;
 }

@@ -142,17 +142,16 @@ int batch_resident_blocks(size_t smem);
 cudaError_t launch_batch(const SweepArgs *insts, const BatchItem *items, int32_t n_items, uint32_t *counter,
                          int grid, size_t smem, bool record, cudaStream_t s);
 
-// Allocation-free batched sweep (see muca_batch_sweep_noalloc in muca.h): descriptors
-// and walkers per item come from the host; the kernel's scratch is a file-scope device
-// array of kNoAllocScratchBytes, looked up on the first call per device.
+// Allocation-free batched sweep (see muca_batch_sweep_noalloc in muca.h): descriptors,
+// walkers per item and the prefix sums of the work items per instance (prefix[0] = 0,
+// prefix[n] = all items, below 2^31) come from the host and travel in the launch
+// parameters; the kernel's only scratch, its work counter, is a file-scope device array
+// of kNoAllocScratchBytes, looked up on the first call per device.
 constexpr int kNoAllocMaxInstances = 64;
 constexpr int kNoAllocMaxDevices = 64;
-constexpr size_t kNoAllocWpbOffset = sizeof(SweepArgs) * kNoAllocMaxInstances;
-constexpr size_t kNoAllocCounterOffset = kNoAllocWpbOffset + sizeof(int32_t) * (2 * kNoAllocMaxInstances + 1);
-constexpr size_t kNoAllocScratchBytes = 8192;
-static_assert(kNoAllocCounterOffset + sizeof(uint32_t) <= kNoAllocScratchBytes, "scratch layout");
-cudaError_t launch_batch_noalloc(const SweepArgs *descs, const int32_t *wpbs, int32_t n, size_t smem, bool record,
-                                 cudaStream_t s);
+constexpr size_t kNoAllocScratchBytes = 256;
+cudaError_t launch_batch_noalloc(const SweepArgs *descs, const int32_t *wpbs, const int32_t *prefix, int32_t n,
+                                 size_t smem, bool record, cudaStream_t s);
 
 // Issue rate of one instruction class (muca_probe.cu, see muca_measure_issue_rate).
 cudaError_t measure_issue_rate(int kind, double *per_second);

@@ -11,31 +11,37 @@ namespace muca {
 namespace {
 
 // ---------------------------------------------------------------------------------
-// Allocation-free variant of the batched kernel.  Its scratch (instance descriptors,
-// walkers per work item, item prefix sums and the work counter) lives in the file-scope
-// array g_noalloc_scratch below instead of memory the library allocates; the work list
-// is derived from the prefix sums, so the caller passes only the instances' own buffers.
+// Allocation-free variant of the batched kernel.  The instance descriptors, walkers per
+// work item and the work list's prefix sums travel by value in the launch parameters
+// (NoAllocLaunch, a few KiB); its one piece of scratch, the work counter, lives in the
+// file-scope array g_noalloc_scratch below instead of memory the library allocates.
+// The work list is derived from the prefix sums, so the caller passes only the
+// instances' own buffers.
 // ---------------------------------------------------------------------------------
+struct NoAllocLaunch {
+    SweepArgs descs[kNoAllocMaxInstances];
+    int32_t wpbs[kNoAllocMaxInstances];
+    int32_t prefix[kNoAllocMaxInstances + 1];   // work items before instance i
+    int32_t n;
+};
+
 template <bool RECORD>
-__global__ void __launch_bounds__(256, 1) batch_noalloc_kernel(const unsigned char *scratch, int32_t n)
+__global__ void __launch_bounds__(256, 1) batch_noalloc_kernel(const __grid_constant__ NoAllocLaunch p,
+                                                               uint32_t *counter)
 {
     extern __shared__ __align__(16) unsigned char smem[];
     __shared__ int32_t s_inst;
     __shared__ int64_t s_wbase;
-    const SweepArgs *descs = reinterpret_cast<const SweepArgs *>(scratch);
-    const int32_t *wpbs = reinterpret_cast<const int32_t *>(scratch + kNoAllocWpbOffset);
-    const int32_t *prefix = wpbs + kNoAllocMaxInstances;
-    uint32_t *counter = reinterpret_cast<uint32_t *>(const_cast<unsigned char *>(scratch) + kNoAllocCounterOffset);
-    const int32_t total = prefix[n];
+    const int32_t total = p.prefix[p.n];
     for (;;) {
         if (threadIdx.x == 0) {
             const int32_t k = (int32_t)atomicAdd(counter, 1u);
             int32_t i = -1;
-            if (k < total) {
+            if (k >= 0 && k < total) {
                 i = 0;
-                while (prefix[i + 1] <= k)
+                while (p.prefix[i + 1] <= k)
                     ++i;
-                s_wbase = (int64_t)(k - prefix[i]) * wpbs[i];
+                s_wbase = (int64_t)(k - p.prefix[i]) * p.wpbs[i];
             }
             s_inst = i;
         }
@@ -45,10 +51,10 @@ __global__ void __launch_bounds__(256, 1) batch_noalloc_kernel(const unsigned ch
         __syncthreads();
         if (i < 0)
             break;
-        const SweepArgs a = descs[i];
+        const SweepArgs a = p.descs[i];
         BatchItem it;
         it.inst = i;
-        it.wpb = wpbs[i];
+        it.wpb = p.wpbs[i];
         it.wbase = wbase;
         switch (a.L) {
         case 8: batch_item<8, RECORD, true>(a, it, smem); break;
@@ -75,9 +81,11 @@ std::mutex g_noalloc_mutex;
 void *g_noalloc_ptr[kNoAllocMaxDevices] = {};
 }  // namespace
 
-cudaError_t launch_batch_noalloc(const SweepArgs *descs, const int32_t *wpbs, int32_t n, size_t smem, bool record,
-                                 cudaStream_t s)
+cudaError_t launch_batch_noalloc(const SweepArgs *descs, const int32_t *wpbs, const int32_t *prefix, int32_t n,
+                                 size_t smem, bool record, cudaStream_t s)
 {
+    if (n < 1 || n > kNoAllocMaxInstances)
+        return cudaErrorInvalidValue;
     int dev = 0;
     cudaError_t err = cudaGetDevice(&dev);
     if (err != cudaSuccess)
@@ -97,33 +105,31 @@ cudaError_t launch_batch_noalloc(const SweepArgs *descs, const int32_t *wpbs, in
         }
         ptr = g_noalloc_ptr[dev];
     }
-    // descriptors, walkers per item, prefix sums and a zero counter, staged on the stack
-    unsigned char host[kNoAllocCounterOffset + sizeof(uint32_t)];
-    std::memset(host, 0, sizeof host);
-    std::memcpy(host, descs, sizeof(SweepArgs) * (size_t)n);
-    int32_t *hw = reinterpret_cast<int32_t *>(host + kNoAllocWpbOffset);
-    int32_t *hp = hw + kNoAllocMaxInstances;
-    hp[0] = 0;
-    for (int32_t i = 0; i < n; ++i) {
-        hw[i] = wpbs[i];
-        hp[i + 1] = hp[i] + (int32_t)((descs[i].W + wpbs[i] - 1) / wpbs[i]);
-    }
-    // pageable source: the copy has left the stack buffer when the call returns
-    err = cudaMemcpyAsync(ptr, host, sizeof host, cudaMemcpyHostToDevice, s);
-    if (err != cudaSuccess)
-        return err;
+    NoAllocLaunch p;
+    std::memset(&p, 0, sizeof p);
+    std::memcpy(p.descs, descs, sizeof(SweepArgs) * (size_t)n);
+    std::memcpy(p.wpbs, wpbs, sizeof(int32_t) * (size_t)n);
+    std::memcpy(p.prefix, prefix, sizeof(int32_t) * (size_t)(n + 1));
+    p.n = n;
     auto kern = record ? batch_noalloc_kernel<true> : batch_noalloc_kernel<false>;
     err = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (err != cudaSuccess)
         return err;
-    int sms = 1, occ = 0;
-    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    int sms = 0, occ = 0;
+    err = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    if (err != cudaSuccess)
+        return err;
     err = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kern, kBatchThreads, smem);
     if (err != cudaSuccess)
         return err;
-    if (occ < 1)
+    if (occ < 1 || sms < 1)
         return cudaErrorInvalidConfiguration;
-    kern<<<sms * occ, kBatchThreads, smem, s>>>(static_cast<const unsigned char *>(ptr), n);
+    // the work counter starts at zero in every call
+    uint32_t *counter = static_cast<uint32_t *>(ptr);
+    err = cudaMemsetAsync(counter, 0, sizeof(uint32_t), s);
+    if (err != cudaSuccess)
+        return err;
+    kern<<<sms * occ, kBatchThreads, smem, s>>>(p, counter);
     return cudaGetLastError();
 }
 

@@ -110,6 +110,9 @@ def test_noalloc_rejects_sizes_beyond_its_limits(env):
         with pytest.raises(M.MucaError) as ex:
             M.muca_batch_sweep_noalloc([r], 0xFFFFFFFF // 256 // (L * L) + 1, True)
         assert ex.value.code == C.MUCA_EINVAL
+        with pytest.raises(M.MucaError) as ex:       # the same buffers twice in one call
+            M.muca_batch_sweep_noalloc([r, r], 1, False)
+        assert ex.value.code == C.MUCA_EINVAL
         r.t0 = 5
         with pytest.raises(M.MucaError):
             M.muca_batch_sweep_noalloc([r], 1, False)
@@ -168,7 +171,7 @@ def test_noalloc_energies_that_do_not_match_the_lattices(env, orc):
     table has zero rows around the grid), flips that would leave the grid are rejected,
     and lattices, energies and histogram equal the oracle's run on the same inputs."""
     torch, M, C = env
-    for L, W, lay, seed in [(16, 64, 0, 31), (32, 100, 1, 32), (24, 40, 0, 33)]:
+    for L, W, lay, seed in [(16, 64, 0, 31), (32, 100, 1, 32), (24, 40, 0, 33), (8, 50, 0, 34), (64, 40, 1, 35)]:
         N = L * L
         with M.Muca(L, W, seed, layout=lay) as m:
             m.set_weights(weights(L, seed))
