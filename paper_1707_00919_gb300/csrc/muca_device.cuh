@@ -88,9 +88,15 @@ constexpr uint32_t kSharedStream = 0xFFFFFFFFu;   // walker word of the site str
 struct PhiloxKeys {
     uint32_t k0[10], k1[10];   // round keys
     uint32_t hi_w, lo_w;       // round-0 product of the walker counter word
+    uint32_t c1;               // counter word 1 (high word of t >> 2) the next two are for
+    uint32_t r1_hi, r1_lo;     // round-1 product of the first word, (hi_w ^ c1 ^ k0) * M0
 };
 
-__device__ __forceinline__ PhiloxKeys make_keys(uint64_t seed, uint32_t walker)
+// Round keys of the seed and the products that depend only on the walker and on counter
+// word 1: with the tag word 0, round 0 turns (c0, c1, walker, 0) into
+// (hi_w ^ c1 ^ k0, lo_w, hi(M0 c0) ^ k1, lo(M0 c0)), so round 1's first product is
+// fixed for as long as c1 is (2^34 attempts).
+__device__ __forceinline__ PhiloxKeys make_keys(uint64_t seed, uint32_t walker, uint32_t c1 = 0)
 {
     PhiloxKeys p;
 #pragma unroll
@@ -101,6 +107,10 @@ __device__ __forceinline__ PhiloxKeys make_keys(uint64_t seed, uint32_t walker)
     const unsigned long long pw = (unsigned long long)0xCD9E8D57u * walker;
     p.hi_w = (uint32_t)(pw >> 32);
     p.lo_w = (uint32_t)pw;
+    p.c1 = c1;
+    const unsigned long long p1 = (unsigned long long)0xD2511F53u * (p.hi_w ^ c1 ^ p.k0[0]);
+    p.r1_hi = (uint32_t)(p1 >> 32);
+    p.r1_lo = (uint32_t)p1;
     return p;
 }
 
@@ -121,6 +131,30 @@ __device__ __forceinline__ uint4 philox_walker(uint32_t c0, uint32_t c1, const P
         const uint32_t n2 = (uint32_t)(p0 >> 32) ^ x3 ^ p.k1[r];
         x0 = n0;
         x1 = (uint32_t)p1;
+        x2 = n2;
+        x3 = (uint32_t)p0;
+    }
+    return make_uint4(x0, x1, x2, x3);
+}
+
+// The same on counter (c0, p.c1, walker, tag 0), with round 1's product of the
+// constant word taken from the keys: one wide multiply fewer per call.
+__device__ __forceinline__ uint4 philox_walker_c1(uint32_t c0, const PhiloxKeys &p)
+{
+    const unsigned long long q = (unsigned long long)0xD2511F53u * c0;
+    const unsigned long long p1 = (unsigned long long)0xCD9E8D57u * ((uint32_t)(q >> 32) ^ p.k1[0]);
+    uint32_t x0 = (uint32_t)(p1 >> 32) ^ p.lo_w ^ p.k0[1];
+    uint32_t x1 = (uint32_t)p1;
+    uint32_t x2 = p.r1_hi ^ (uint32_t)q ^ p.k1[1];
+    uint32_t x3 = p.r1_lo;
+#pragma unroll
+    for (int r = 2; r < 10; ++r) {
+        const unsigned long long p0 = (unsigned long long)0xD2511F53u * x0;
+        const unsigned long long pp = (unsigned long long)0xCD9E8D57u * x2;
+        const uint32_t n0 = (uint32_t)(pp >> 32) ^ x1 ^ p.k0[r];
+        const uint32_t n2 = (uint32_t)(p0 >> 32) ^ x3 ^ p.k1[r];
+        x0 = n0;
+        x1 = (uint32_t)pp;
         x2 = n2;
         x3 = (uint32_t)p0;
     }
@@ -350,6 +384,26 @@ struct PhiloxSource {
         return make_uint4(min(rw.x, 0xFFFFFFFEu), min(rw.y, 0xFFFFFFFEu), min(rw.z, 0xFFFFFFFEu),
                           min(rw.w, 0xFFFFFFFEu));
     }
+    __device__ __forceinline__ void advance() const {}
+};
+
+// The same for a row whose Philox blocks all have counter word 1 equal to pk->c1.  The
+// words of the row's first block are computed during the previous row (advance(), called
+// by process_row during its last block) and kept in *carry, so that a new row does not
+// start by waiting for a whole Philox evaluation.
+template <int L>
+struct PhiloxSourceC1 {
+    uint32_t blk;            // counter word 0 of column 0's block
+    const PhiloxKeys *pk;
+    uint4 *carry;            // clamped words of block blk, then of the next row's first block
+    __device__ __forceinline__ static uint4 words(uint32_t b, const PhiloxKeys &k)
+    {
+        const uint4 rw = philox_walker_c1(b, k);
+        return make_uint4(min(rw.x, 0xFFFFFFFEu), min(rw.y, 0xFFFFFFFEu), min(rw.z, 0xFFFFFFFEu),
+                          min(rw.w, 0xFFFFFFFEu));
+    }
+    __device__ __forceinline__ uint4 get(int xb) const { return xb == 0 ? *carry : words(blk + (uint32_t)(xb / 4), *pk); }
+    __device__ __forceinline__ void advance() const { *carry = words(blk + (uint32_t)(L / 4), *pk); }
 };
 
 // MASKED: only the attempts x in [x_begin, x_end) happen (a launch that starts or ends
@@ -401,6 +455,8 @@ __device__ __forceinline__ void process_row(const uint32_t (&U)[L / 8], uint32_t
 #pragma unroll
     for (int xb = 0; xb < L; xb += 4) {
         const uint4 rw = src.get(xb);
+        if (xb == L - 4)
+            src.advance();
         const uint32_t words[4] = {rw.x, rw.y, rw.z, rw.w};
 #pragma unroll
         for (int u = 0; u < 4; ++u) {
@@ -445,6 +501,196 @@ __device__ __forceinline__ void process_row(const uint32_t (&U)[L / 8], uint32_t
     E = Eres;
 }
 
+// ---------------------------------------------------------------------------------
+// Continuous attempt stream over whole rows (whole-sweep launches).  The two threshold
+// candidates of every attempt are loaded two attempts ahead, across row ends as well:
+// the first two sites of the next row have as neighbours the current row's first two
+// sites (final after its attempts 0 and 1) and rows that the current row does not
+// change, so their counts, and the candidates of the next row's attempts 0 and 1, are
+// known during the current row's attempts L - 2 and L - 1.  A new row then starts with
+// its first two decisions ready instead of waiting for its counts and loads.
+// ---------------------------------------------------------------------------------
+template <int L, int STRIDE>
+struct AttemptStream {
+    static constexpr uint32_t kD2 = 8u * STRIDE, kDJ = STRIDE;   // row step 4 STRIDE (2 - k) = kD2 - kDJ J
+    uint32_t E;                      // table row address of the current energy
+    bool prev_acc;                   // the previous attempt flipped
+    uint32_t T0n, T1n, T0nn, T1nn;   // candidates of the next two attempts
+    uint32_t d0_cur, d1_cur, d0_next, d1_next;
+
+    // Counts of the row (U above, C, D below) in nibble fields: K0 if the left
+    // neighbour did not flip, K1 if it did.
+    __device__ __forceinline__ static void counts(const uint32_t (&U)[L / 8], const uint32_t (&C)[L / 8],
+                                                  const uint32_t (&D)[L / 8], uint32_t (&K0)[L / 8],
+                                                  uint32_t (&K1)[L / 8])
+    {
+        constexpr int NW = L / 8;
+#pragma unroll
+        for (int i = 0; i < NW; ++i) {
+            const uint32_t cr = __funnelshift_r(C[i], C[(i + 1) % NW], 4);
+            const uint32_t cl = __funnelshift_l(C[(i + NW - 1) % NW], C[i], 4);
+            const uint32_t kb = (U[i] ^ C[i]) + (D[i] ^ C[i]) + (C[i] ^ cr);
+            const uint32_t h0 = C[i] ^ cl;
+            K0[i] = kb + h0;
+            K1[i] = kb + 0x11111111u - h0;
+        }
+    }
+
+    // First row of a launch: the candidates of its attempts 0 and 1.
+    __device__ __forceinline__ void start(const uint32_t (&U)[L / 8], const uint32_t (&C)[L / 8],
+                                          const uint32_t (&D)[L / 8], uint32_t E0)
+    {
+        uint32_t K0[L / 8], K1[L / 8];
+        counts(U, C, D, K0, K1);
+        const uint32_t J0a = field_x4(K0[0], 0), J0b = field_x4(K0[0], 1), J1b = field_x4(K1[0], 1);
+        E = E0;
+        prev_acc = false;
+        d0_cur = d1_cur = kD2 - kDJ * J0a;
+        d0_next = kD2 - kDJ * J0b;
+        d1_next = kD2 - kDJ * J1b;
+        T0n = T1n = lds_u32(E + J0a);
+        T0nn = lds_u32(E + J0b);
+        T1nn = lds_u32(E + d0_cur + J1b);
+    }
+
+    // One row (U above, C updated in place, D below, D2 the row below D); on return the
+    // candidates of the next row's attempts 0 and 1 are loaded.
+    template <bool RECORD, class Src>
+    __device__ __forceinline__ void row(const uint32_t (&U)[L / 8], uint32_t (&C)[L / 8], const uint32_t (&D)[L / 8],
+                                        const uint32_t (&D2)[L / 8], const Src &src)
+    {
+        constexpr int NW = L / 8;
+        uint32_t K0[NW], K1[NW];
+        counts(U, C, D, K0, K1);
+        uint32_t K0n = 0u, K1n = 0u;   // word 0 of the next row's counts (fields 0 and 1 used)
+        const uint32_t hr_last = ((C[NW - 1] >> 28) ^ C[0]) & 1u;
+        const uint32_t adj_if_flip = hr_last ? (uint32_t)-4 : 4u;
+        uint32_t adj_last = 0u;
+        uint32_t Eres = E;
+#pragma unroll
+        for (int xb = 0; xb < L; xb += 4) {
+            const uint4 rw = src.get(xb);
+            if (xb == L - 4) {
+                src.advance();
+                // the current row's sites 0 and 1 are final: the next row's first counts
+                const uint32_t crn = __funnelshift_r(D[0], D[1 % NW], 4);
+                const uint32_t cln = __funnelshift_l(D[NW - 1], D[0], 4);
+                const uint32_t kbn = (C[0] ^ D[0]) + (D2[0] ^ D[0]) + (D[0] ^ crn);
+                const uint32_t h0n = D[0] ^ cln;
+                K0n = kbn + h0n;
+                K1n = kbn + 0x11111111u - h0n;
+            }
+            const uint32_t words[4] = {rw.x, rw.y, rw.z, rw.w};
+#pragma unroll
+            for (int u = 0; u < 4; ++u) {
+                const int x = xb + u;
+                const uint32_t dsel = prev_acc ? d1_cur : d0_cur;
+                const uint32_t Eacc = Eres + dsel;
+                const bool c0 = words[u] < T0n, c1 = words[u] < T1n;
+                const bool acc = prev_acc ? c1 : c0;
+                const uint32_t Epost = acc ? Eacc : Eres;
+                C[x >> 3] ^= acc ? (1u << (4 * (x & 7))) : 0u;
+                if (x == 0)
+                    adj_last = acc ? adj_if_flip : 0u;
+                if (RECORD)
+                    hist_add_one(Epost);
+                else
+                    pad_add_one<STRIDE>(Epost);
+                // candidates of attempt x + 2 (in this row or the next) for both outcomes
+                // of attempt x + 1
+                uint32_t J0c, J1c;
+                if (x + 2 < L) {
+                    J0c = field_x4(K0[(x + 2) >> 3], (x + 2) & 7);
+                    J1c = field_x4(K1[(x + 2) >> 3], (x + 2) & 7);
+                    if (x + 2 == L - 1) {
+                        J0c += adj_last;
+                        J1c += adj_last;
+                    }
+                } else if (x + 2 == L) {
+                    J0c = J1c = field_x4(K0n, 0);   // site 0: its left neighbour comes later
+                } else {
+                    J0c = field_x4(K0n, 1);
+                    J1c = field_x4(K1n, 1);
+                }
+                T0n = T0nn;
+                T1n = T1nn;
+                const uint32_t a0 = acc ? Eacc + J0c : Eres + J0c;
+                const uint32_t a1 = acc ? Eacc + d1_next + J1c : Eres + d0_next + J1c;
+                T0nn = lds_u32(a0);
+                T1nn = lds_u32(a1);
+                d0_cur = d0_next;
+                d1_cur = d1_next;
+                d0_next = kD2 - kDJ * J0c;
+                d1_next = kD2 - kDJ * J1c;
+                Eres = Epost;
+                prev_acc = acc;
+            }
+        }
+        E = Eres;
+    }
+};
+
+// nsweeps whole sweeps of one walker from Philox block blk (column 0 of row 0); U, C, D
+// hold rows L - 1, 0 and 1 on entry and are left in the same state on exit.
+// Counter word 1 must stay at pk.c1 for the whole range.  The row below the next one is
+// loaded from shared memory when a row starts (the current row does not change it), and
+// the next row's first Philox block is computed during the current row.
+template <int L, bool RECORD, int STRIDE>
+__device__ __forceinline__ void whole_sweeps_c1(const SmemRows<L> &rows, uint32_t (&U)[L / 8], uint32_t (&C)[L / 8],
+                                                uint32_t (&D)[L / 8], uint32_t &E, uint64_t blk, uint64_t nsweeps,
+                                                const PhiloxKeys &pk)
+{
+    constexpr int NW = L / 8;
+    uint32_t b = (uint32_t)blk;
+    uint4 carry = PhiloxSourceC1<L>::words(b, pk);
+    AttemptStream<L, STRIDE> st;
+    st.start(U, C, D, E);
+    for (uint64_t s = 0; s < nsweeps; ++s) {
+#pragma unroll 1
+        for (int y = 0; y < L; ++y) {
+            const int y2 = (y + 2 < L) ? y + 2 : y + 2 - L;
+            uint32_t D2[NW];
+            rows.load(y2, D2);
+            const PhiloxSourceC1<L> src{b, &pk, &carry};
+            st.template row<RECORD>(U, C, D, D2, src);
+            rows.store(y, C);
+#pragma unroll
+            for (int i = 0; i < NW; ++i) {
+                U[i] = C[i];
+                C[i] = D[i];
+                D[i] = D2[i];
+            }
+            b += (uint32_t)(L / 4);
+        }
+    }
+    E = st.E;
+}
+
+// The same with the general generator (any counter range).
+template <int L, bool RECORD, int STRIDE>
+__device__ __forceinline__ void whole_sweeps(const SmemRows<L> &rows, uint32_t (&U)[L / 8], uint32_t (&C)[L / 8],
+                                             uint32_t (&D)[L / 8], uint32_t &E, uint64_t blk, uint64_t nsweeps,
+                                             const PhiloxKeys &pk)
+{
+    constexpr int NW = L / 8;
+    for (uint64_t s = 0; s < nsweeps; ++s) {
+#pragma unroll 1
+        for (int y = 0; y < L; ++y) {
+            const PhiloxSource src{blk, &pk};
+            process_row<L, RECORD, false, PhiloxSource, STRIDE>(U, C, D, E, src);
+            rows.store(y, C);
+            const int y2 = (y + 2 < L) ? y + 2 : y + 2 - L;
+#pragma unroll
+            for (int i = 0; i < NW; ++i) {
+                U[i] = C[i];
+                C[i] = D[i];
+            }
+            rows.load(y2, D);
+            blk += (uint64_t)(L / 4);
+        }
+    }
+}
+
 // One block's share of a launch: walkers wbase .. wbase + wpb - 1 of the instance in
 // `a` (threads tid >= wpb idle), all of the launch's whole sweeps.  Shared memory:
 // the table, then the rows of the wpb walkers.  Every thread of the block calls it.
@@ -452,7 +698,10 @@ __device__ __forceinline__ void process_row(const uint32_t (&U)[L / 8], uint32_t
 // compile-time layout get it folded, the batched kernels pass it at run time.  GUARD
 // adds kTableGuard zero rows on both sides of the table, for energies that come from the
 // caller and need not match the lattices (the library's own energies always do).
-template <int L, bool RECORD, bool PARTIAL = false, bool GUARD = false, int STRIDE = kTableStride>
+// C1_ONLY: the caller guarantees that counter word 1 (t >> 34) is the same for every
+// attempt of the launch, so only the generator that relies on it is compiled in.
+template <int L, bool RECORD, bool PARTIAL = false, bool GUARD = false, int STRIDE = kTableStride,
+          bool C1_ONLY = false>
 __device__ __forceinline__ void sweep_block(const SweepArgs &a, int64_t wbase, int wpb, unsigned char *smem,
                                             const int LAYOUT)
 {
@@ -521,33 +770,22 @@ __device__ __forceinline__ void sweep_block(const SweepArgs &a, int64_t wbase, i
     __syncthreads();
 
     if (active) {
-        const PhiloxKeys pk = make_keys(a.seed, a.walker0 + (uint32_t)w);
+        const PhiloxKeys pk = make_keys(a.seed, a.walker0 + (uint32_t)w, (uint32_t)(a.t0 >> 34));
         const uint32_t tbase = (uint32_t)__cvta_generic_to_shared(sTab) + G * STRIDE * 4u;
         uint32_t U[NW], C[NW], D[NW];
         uint32_t E = tbase + (uint32_t)e * (4u * STRIDE);
         if (!PARTIAL) {
-            // whole sweeps from a sweep boundary
-            uint64_t blk = a.t0 >> 2;
-            const uint64_t nsweeps = a.n / (uint64_t)N;
+            // whole sweeps from a sweep boundary; counter word 1 (t >> 34) is the same for
+            // every attempt of the launch except in the rare launch that crosses a step
+            // of it, which takes the general generator throughout (kernels whose launches
+            // never cross one compile only the first)
             rows.load(L - 1, U);
             rows.load(0, C);
             rows.load(1, D);
-            for (uint64_t s = 0; s < nsweeps; ++s) {
-#pragma unroll 1
-                for (int y = 0; y < L; ++y) {
-                    const PhiloxSource src{blk, &pk};
-                    process_row<L, RECORD, false, PhiloxSource, STRIDE>(U, C, D, E, src);
-                    rows.store(y, C);
-                    const int y2 = (y + 2 < L) ? y + 2 : y + 2 - L;
-#pragma unroll
-                    for (int i = 0; i < NW; ++i) {
-                        U[i] = C[i];
-                        C[i] = D[i];
-                    }
-                    rows.load(y2, D);
-                    blk += (uint64_t)(L / 4);
-                }
-            }
+            if (C1_ONLY || (a.t0 >> 34) == ((a.t0 + a.n - 1) >> 34))
+                whole_sweeps_c1<L, RECORD, STRIDE>(rows, U, C, D, E, a.t0 >> 2, a.n / (uint64_t)N, pk);
+            else
+                whole_sweeps<L, RECORD, STRIDE>(rows, U, C, D, E, a.t0 >> 2, a.n / (uint64_t)N, pk);
         } else {
             // any attempt range: rows cut by the launch's start or end run masked
             uint64_t t = a.t0;

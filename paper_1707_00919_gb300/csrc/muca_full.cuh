@@ -15,7 +15,9 @@ template <int L, int LAYOUT, bool RECORD, bool PARTIAL>
 __global__ void __launch_bounds__(256, 1) sweep_full_kernel(const SweepArgs a)
 {
     extern __shared__ __align__(16) unsigned char smem[];
-    sweep_block<L, RECORD, PARTIAL>(a, (int64_t)blockIdx.x * blockDim.x, blockDim.x, smem, LAYOUT);
+    // launch_sweep splits launches at the steps of counter word 1
+    sweep_block<L, RECORD, PARTIAL, false, kTableStride, true>(a, (int64_t)blockIdx.x * blockDim.x, blockDim.x, smem,
+                                                               LAYOUT);
 }
 
 template <int L, int LAYOUT, bool RECORD, bool PARTIAL>

@@ -359,6 +359,17 @@ cudaError_t launch_sweep(const SweepArgs &a, int wpb, bool record, cudaStream_t 
         return cudaSuccess;
     if (!has_full_kernel(a.L) || !g_use_full_kernel)
         return launch_generic(a, wpb, record, s);
+    // the whole-sweep kernels keep Philox counter word 1 (t >> 34) fixed within a launch:
+    // a range that crosses a multiple of 2^34 runs as two launches
+    const uint64_t step = a.t0 >> 34;
+    if (((a.t0 + a.n - 1) >> 34) != step) {
+        SweepArgs first = a, second = a;
+        first.n = ((step + 1) << 34) - a.t0;
+        second.t0 = a.t0 + first.n;
+        second.n = a.n - first.n;
+        cudaError_t err = launch_full(first, wpb, record, s);
+        return err != cudaSuccess ? err : launch_sweep(second, wpb, record, s);
+    }
     return launch_full(a, wpb, record, s);
 }
 

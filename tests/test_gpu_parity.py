@@ -120,6 +120,38 @@ def test_partial_sweeps_bit_exact(muca_mod, orc, layout, L):
     assert np.array_equal(lat, s) and np.array_equal(e, eo) and np.array_equal(H, Ho)
 
 
+@pytest.mark.parametrize("layout", [0, 1])
+@pytest.mark.parametrize("L", [8, 24, 32, 64])
+def test_counter_high_word_boundary(muca_mod, orc, layout, L):
+    """Attempt counters around t = 2^34, where Philox counter word 1 (the high word of
+    t >> 2) steps from 0 to 1: whole sweeps, a row and partial launches across the step
+    equal the oracle (the sweep kernels take round 1's product of the constant word from
+    the keys only while word 1 stays at the launch's first value)."""
+    W = 40
+    N = L * L
+    lnW = rand_weights(L, 2, 0.3)
+    t0 = (2**34 // N - 2) * N                         # two sweeps before the step
+    with muca_mod.Muca(L, W, 9, layout=layout, walkers_per_block=32) as m:
+        m.set_weights(lnW)
+        m.set_attempt_counter(t0)
+        m.reset_histogram()
+        m.sweep(5, True)                                # crosses 2^34 in one launch
+        m.attempts(3 * L + 5, True)                     # partial launches after it
+        m.attempts(N - 7, False)
+        m.set_attempt_counter(2**34 - L - 3)            # a partial launch across the step
+        m.attempts(2 * L + 9, True)
+        lat, e, H, t = m.get_lattice(), m.get_energies(), m.get_histogram(), m.attempt_counter
+    s, eo = orc.init(L, 9, W)
+    T = orc.build_table(L, lnW)
+    Ho = np.zeros(N + 1, dtype=np.uint64)
+    orc.run(L, 9, s, eo, T, t0, 5 * N, True, Ho)
+    orc.run(L, 9, s, eo, T, t0 + 5 * N, 3 * L + 5, True, Ho)
+    orc.run(L, 9, s, eo, T, t0 + 5 * N + 3 * L + 5, N - 7, False)
+    orc.run(L, 9, s, eo, T, 2**34 - L - 3, 2 * L + 9, True, Ho)
+    assert t == 2**34 - L - 3 + 2 * L + 9
+    assert np.array_equal(lat, s) and np.array_equal(e, eo) and np.array_equal(H, Ho)
+
+
 def test_all_accept_and_quench_limits(muca_mod, orc):
     L, W = 8, 64
     N = L * L
