@@ -11,10 +11,12 @@ Reported:
                histogram read, flatness test and Eq. (4) recursion), device-timed with
                CUDA events, L2 flushed between steps;
   time_to_flat wall time of muca_iterate_until_flat from ln W = 0 until min/mean >= 0.8;
-  e2e          the same steps through the Python binding with host weights in and the
-               host histogram out (copies inside the timed region), host wall clock;
-  roofline     the recorded-sweep kernel against the integer-issue ceiling;
-  cpu_baseline the C oracle on the host cores for one step of the same workload.
+  e2e          the same steps through the C ABI with host weights in and the host
+               histogram out (copies inside the timed region), host wall clock;
+  roofline     the recorded-sweep kernel against the integer-issue ceiling (and against
+               the measured issue rate of a balanced integer mix);
+  cpu_baseline the C oracle on the host cores: one step of the same workload on all cores
+               and on one thread, and its whole weight iteration to a flat histogram.
 
 python bench.py [--gpus N] [--steps K] [--warmup W] [--impl native|reference]
 """
@@ -47,7 +49,7 @@ OPS_PER_ATTEMPT = 35.0
 # Warp instructions the recorded whole-sweep kernel issues per attempt and warp (ncu
 # count, profiles/sweep_full_kernel_L32_W16384_int8.md): converts an instruction issue
 # rate into this roofline's algorithmic operations.
-INSTR_PER_ATTEMPT = 34.0
+INSTR_PER_ATTEMPT = 33.6
 WORKLOAD = (f"muca2d_ising_L{L_SIDE}_W{WALKERS}_int8_therm{THERM_SWEEPS}_rec{SWEEPS_PER_ITER}")
 
 
@@ -139,6 +141,7 @@ class ClockSampler:
         self.dev = device_index
         self.proc = None
         self.lines = []
+        self.times = []
 
     def __enter__(self):
         try:
@@ -154,6 +157,7 @@ class ClockSampler:
     def _read(self):
         for line in self.proc.stdout:
             self.lines.append(line.strip())
+            self.times.append(time.perf_counter())
 
     def __exit__(self, *exc):
         if self.proc is not None:
@@ -162,6 +166,9 @@ class ClockSampler:
                 self.proc.wait(timeout=5)
             except subprocess.TimeoutExpired:
                 self.proc.kill()
+
+    def count_between(self, t0: float, t1: float) -> int:
+        return sum(1 for t in self.times if t0 <= t <= t1)
 
     def summary(self):
         sm, mx, reasons = [], None, set()
@@ -267,6 +274,81 @@ def cpu_baseline(lnW, walkers: int, cores: int | None = None):
     return attempts / busy, len(jobs), wall
 
 
+def _oracle_worker(conn, L, seed, w0, nw):
+    """Holds one shard of walkers for the oracle's weight iteration: for each message
+    (thresholds, t0, n_therm, n_rec) it runs the shard's thermalization and recorded
+    attempts and sends back the shard's histogram."""
+    from oracle import oracle
+    s, e = oracle.init(L, seed, nw, walker0=w0)
+    conn.send("ready")
+    while True:
+        msg = conn.recv()
+        if msg is None:
+            break
+        T, t0, n_therm, n_rec = msg
+        oracle.run(L, seed, s, e, T, t0, n_therm, False, None, walker0=w0)
+        conn.send(oracle.run(L, seed, s, e, T, t0 + n_therm, n_rec, True, None, walker0=w0))
+
+
+def cpu_time_to_flat(walkers: int, cores: int | None = None, max_iterations: int = MAX_ITERATIONS):
+    """The oracle's weight iteration of the headline workload from ln W = 0 to
+    min/mean >= 0.8: walkers split over host processes (one shard each, kept between
+    iterations), histograms summed, the oracle's flatness test, Eq. (4) recursion and
+    table on the host.  Returns (seconds, iterations, converged, ln W, processes); the
+    clock starts once the shards hold their initial lattices."""
+    import multiprocessing as mp
+    import numpy as np
+    from oracle import oracle
+    oracle.build()
+    N = L_SIDE * L_SIDE
+    cores = cores or os.cpu_count() or 1
+    shard = (walkers + cores - 1) // cores
+    ctx = mp.get_context("spawn")
+    procs, conns = [], []
+    for c in range(cores):
+        w0, nw = c * shard, min(shard, walkers - c * shard)
+        if nw <= 0:
+            break
+        a, b = ctx.Pipe()
+        p = ctx.Process(target=_oracle_worker, args=(b, L_SIDE, SEED, w0, nw), daemon=True)
+        p.start()
+        procs.append(p)
+        conns.append(a)
+    for c in conns:
+        c.recv()
+    lnW = np.zeros(N + 1)
+    t, it, converged = 0, 0, False
+    n_therm, n_rec = THERM_SWEEPS * N, SWEEPS_PER_ITER * N
+    t0 = time.perf_counter()
+    while it < max_iterations:
+        T = oracle.build_table(L_SIDE, lnW)
+        for c in conns:
+            c.send((T, t, n_therm, n_rec))
+        H = np.zeros(N + 1, dtype=np.uint64)
+        for c in conns:
+            H += c.recv()
+        t += n_therm + n_rec
+        it += 1
+        if oracle.min_over_mean(L_SIDE, H) >= 0.8:
+            converged = True
+            break
+        oracle.update_weights(L_SIDE, lnW, H)
+    seconds = time.perf_counter() - t0
+    for c in conns:
+        c.send(None)
+    for p in procs:
+        p.join(timeout=10)
+    return seconds, it, converged, lnW, len(procs)
+
+
+def cpu_single_thread(lnW, walkers: int = 512):
+    """The oracle on one host thread: one step (thermalization + recorded sweeps) of
+    `walkers` walkers; returns attempts/s."""
+    N = L_SIDE * L_SIDE
+    busy, _ = _oracle_shard((L_SIDE, SEED, 0, walkers, list(lnW), 0, THERM_SWEEPS * N, SWEEPS_PER_ITER * N))
+    return walkers * (THERM_SWEEPS + SWEEPS_PER_ITER) * N / busy
+
+
 # ----------------------------------------------------------------------------------
 # native arm
 # ----------------------------------------------------------------------------------
@@ -290,6 +372,10 @@ def run_native(args):
     seed = SEED + rank                              # independent simulation per GPU
     m = M.Muca(L_SIDE, WALKERS, seed, layout=M.MUCA_LAYOUT_INT8, stream=stream)
 
+    # clocks sampled from here to the end of the end-to-end steps: the whole stretch runs
+    # the same kernels (time to flat, warm-up, timed and end-to-end steps)
+    clocks = ClockSampler(dev).__enter__()
+
     # ---- time to flat histogram (from ln W = 0) ----
     params = M.make_params(therm_sweeps=THERM_SWEEPS, sweeps_per_iter=SWEEPS_PER_ITER,
                            max_iterations=MAX_ITERATIONS)
@@ -301,6 +387,7 @@ def run_native(args):
     ttf = max_over_ranks(dist, ttf)
 
     lnW = m.get_weights()
+    ln_w_flat = lnW.copy()
     attempts_per_step = WALKERS * (THERM_SWEEPS + SWEEPS_PER_ITER) * N
 
     # ---- the same, with the recursion, stop test and table build on the device ----
@@ -313,10 +400,14 @@ def run_native(args):
         same_weights = bool(np.array_equal(md.get_weights(), lnW))
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
 
+    flat = [False]
+
     def step(ev=None):
-        """One weight iteration through the public API; ev = four CUDA events on the
-        instance's stream: step start, before the recorded sweeps, after them, and
-        after the host recursion (so a step's time includes the host work)."""
+        """One weight iteration through the C ABI (table build and upload, thermalization,
+        zeroed histogram, recorded sweeps, histogram read, the min/mean flatness test and
+        the Eq. (4) recursion, muca_flatness and muca_update_weights); ev = four CUDA
+        events on the instance's stream: step start, before the recorded sweeps, after
+        them, and after the host recursion (so a step's time includes the host work)."""
         if ev:
             ev[0].record(stream)
         m.set_weights(lnW)
@@ -328,8 +419,8 @@ def run_native(args):
         if ev:
             ev[2].record(stream)
         H = m.get_histogram()
-        vis = H > 0
-        lnW[vis] -= np.log(H[vis].astype(np.float64))
+        flat[0] = M.muca_flatness(L_SIDE, H)["min_over_mean"] >= 0.8
+        M.muca_update_weights(L_SIDE, lnW, H)
         if ev:
             ev[3].record(stream)
         return H
@@ -346,13 +437,14 @@ def run_native(args):
     evs = [[torch.cuda.Event(enable_timing=True) for _ in range(4)] for _ in range(args.steps)]
     barrier(dist)
     torch.cuda.synchronize()
-    with ClockSampler(dev) as clocks:
-        for k in range(args.steps):
-            step(evs[k])
-            with torch.cuda.stream(stream):
-                flush.zero_()
-        stream.synchronize()
-        torch.cuda.synchronize()
+    t_timed0 = time.perf_counter()
+    for k in range(args.steps):
+        step(evs[k])
+        with torch.cuda.stream(stream):
+            flush.zero_()
+    stream.synchronize()
+    torch.cuda.synchronize()
+    t_timed1 = time.perf_counter()
     torch.cuda.nvtx.range_pop()
     step_ms = [evs[k][0].elapsed_time(evs[k][3]) for k in range(args.steps)]
     therm_ms = [evs[k][0].elapsed_time(evs[k][1]) for k in range(args.steps)]
@@ -368,6 +460,10 @@ def run_native(args):
         step()
     torch.cuda.synchronize()
     e2e_s = max_over_ranks(dist, time.perf_counter() - t0)
+    clocks.__exit__(None, None, None)
+    clock_summary = clocks.summary()
+    clock_summary["timed_region_samples"] = clocks.count_between(t_timed0, t_timed1)
+    clock_summary["window"] = "time to flat, warm-up, timed and end-to-end steps"
 
     value = ws * attempts_per_step * args.steps / total_s
     e2e_value = ws * attempts_per_step * args.steps / e2e_s
@@ -425,6 +521,10 @@ def run_native(args):
                      "ops_per_attempt": OPS_PER_ATTEMPT,
                      "peak_basis": f"{sm_count} SMs x 4 issue slots x 32 lanes x {sm_max_mhz:.0f} MHz",
                      "measured_issue_tops": {k: round(v, 3) for k, v in probe.items()},
+                     # the same achieved rate against the measured issue rate of a balanced
+                     # integer mix (three-input XOR and multiply-add alternating, 16 warps per
+                     # sub-partition): what the hardware sustains for such a mix
+                     "frac_of_measured_mixed_issue": achieved_tops / probe["xor3_imad_alternating"],
                      "single_warp_issue_frac": one_warp_frac,
                      "measured_philox_words_per_s": philox_words,
                      # lattice traffic of the same launch against HBM (not the bound)
@@ -433,7 +533,7 @@ def run_native(args):
                              "peak_gbs": peaks.get("hbm_gbs"),
                              "frac": (lattice_bytes / rec_launch_s / 1e9 / peaks["hbm_gbs"])
                              if peaks.get("hbm_gbs") else None}},
-        "clocks": clocks.summary(),
+        "clocks": clock_summary,
     }
     m.close()
 
@@ -463,6 +563,16 @@ def run_native(args):
         result["cpu_baseline"] = {"value": rate, "unit": "attempts/s", "cores": cores, "kind": "oracle",
                                   "sample": f"one step ({THERM_SWEEPS}+{SWEEPS_PER_ITER} sweeps) of all "
                                             f"{WALKERS} walkers, split over {cores} processes ({wall:.1f} s)"}
+        result["cpu_baseline"]["single_thread_attempts_per_s"] = cpu_single_thread(lnW)
+        result["cpu_baseline"]["single_thread_sample"] = (f"one step of 512 walkers on one host thread")
+        if not args.no_cpu_time_to_flat:
+            secs, its, conv, lnW_cpu, procs = cpu_time_to_flat(WALKERS)
+            result["cpu_baseline"].update({
+                "time_to_flat_s": secs, "time_to_flat_iterations": its, "time_to_flat_flat": conv,
+                "time_to_flat_processes": procs,
+                "time_to_flat_identical_weights": bool(np.array_equal(lnW_cpu, ln_w_flat)),
+                "time_to_flat_sample": f"the whole iteration from ln W = 0 ({WALKERS} walkers, "
+                                       f"{THERM_SWEEPS}+{SWEEPS_PER_ITER} sweeps per iteration) on {procs} processes"})
     if rank == 0:
         print(json.dumps(result))
     if dist is not None:
@@ -908,6 +1018,8 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["native", "reference"], default="native")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-cpu-time-to-flat", action="store_true",
+                    help="skip the oracle's whole weight iteration (about a minute on 16 host cores)")
     ap.add_argument("--workload", choices=["headline", "batch", "serve", "fliptime", "convergence", "production",
                                            "traces"],
                     default="headline")
