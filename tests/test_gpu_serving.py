@@ -1,6 +1,7 @@
 """Serving with continuous batching: requests of different L and walker counts arrive
 while others run, are admitted under a memory budget and iterated together; each result
-must equal the same request run alone (muca_iterate_until_flat), bit for bit."""
+must equal the same request run alone (muca_iterate_until_flat), bit for bit, and the
+oracle's weight iteration of the same request (Sec. 2.2, Eq. 4)."""
 import numpy as np
 import pytest
 
@@ -26,7 +27,7 @@ def params(M, S):
     return M.make_params(therm_sweeps=31, sweeps_per_iter=S, max_iterations=400)
 
 
-def test_requests_alone_and_in_the_mix_agree(M):
+def test_requests_alone_and_in_the_mix_agree(M, orc):
     alone = []
     for L, W, seed, S in SPECS:
         with M.Muca(L, W, seed) as m:
@@ -63,6 +64,20 @@ def test_requests_alone_and_in_the_mix_agree(M):
             assert st.seconds_total >= st.seconds_queued >= 0.0
         att, sec, steps, used = srv.totals()
         assert used == 0 and att > 0
+        # two served requests of different L against the oracle's iteration: iteration
+        # count, last stop metric and final ln W bit for bit
+        for k in (0, 4):
+            L, W, seed, S = SPECS[k]
+            rid = dict(ids)[k]
+            s, e = orc.init(L, seed, W)
+            lnW = np.zeros(L * L + 1)
+            p = orc.make_params(schedule=0, stop_rule=0, flat_threshold=0.8, therm_sweeps=31,
+                                sweeps_per_iter=S, max_iterations=400)
+            res, _, _, _ = orc.iterate(L, seed, s, e, lnW, 0, p)
+            st = srv.status(rid)
+            assert st.stats.iterations == res.iterations and bool(st.stats.converged) == bool(res.converged)
+            assert st.stats.last_metric == res.last_metric
+            assert np.array_equal(srv.weights(rid, L * L + 1), lnW), (L, W)
 
 
 def test_server_rejects_bad_requests(M):
