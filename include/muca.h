@@ -134,9 +134,9 @@ typedef struct {
  * (Eq. (7) then gives way to the growth rule) and the previous N_updates.  With
  * params.resume = 1 a run stopped by max_iterations or the deadline, or restored from a
  * checkpoint, continues the schedule as one uninterrupted call would have.
- * muca_iterate_device and muca_batch_iterate (fixed-sweep schedule) keep and continue the
- * same state (the previous range of the Kullback-Leibler reference); served requests
- * start afresh (muca_server_submit rejects resume = 1). */
+ * muca_iterate_device (fixed-sweep schedule) and muca_batch_iterate (both schedules) keep
+ * and continue the same state; served requests start afresh (muca_server_submit rejects
+ * resume = 1). */
 
 /* Statistics of a weight iteration. */
 typedef struct {
@@ -395,10 +395,13 @@ int muca_batch_destroy(muca_batch_t b);
  * batched launch (more if the 32-bit per-block counts require it).  Asynchronous. */
 int muca_batch_sweep(muca_batch_t b, uint64_t n_sweeps, int record);
 
-/* The weight iteration of muca_iterate_until_flat for every member at once (fixed-sweep
- * schedule only).  Each iteration is one replay of a CUDA graph (table uploads,
- * thermalization launch, zeroed histograms, recording launch, histogram reads); a member
- * leaves the work list when its histogram is flat or it reached max_iterations.
+/* The weight iteration of muca_iterate_until_flat for every member at once (either
+ * schedule; with MUCA_SCHEDULE_PAPER each member follows Eq. (7) from its own visited
+ * ranges, and launches may start and end inside sweeps).  Each iteration is one replay of
+ * a CUDA graph (table uploads, thermalization launch, zeroed histograms, recording
+ * launch, histogram reads), or, when a member records more than 0xFFFFFFFF / 256
+ * attempts per walker, the same steps issued directly with several recording launches;
+ * a member leaves the work list when its histogram is flat or it reached max_iterations.
  * stats[i] (may be NULL) receives member i's result, seconds being the wall time until
  * its last iteration finished.  Returns MUCA_OK if every member became flat, else
  * MUCA_ENOTCONVERGED or MUCA_ETIMEOUT. */
@@ -428,7 +431,7 @@ typedef struct {
     uint64_t seed;
     int32_t layout;              /* MUCA_LAYOUT_INT8 or MUCA_LAYOUT_PACKED                 */
     int32_t walkers_per_block;   /* 0 = from occupancy                                     */
-    muca_params params;          /* fixed-sweep schedule                                   */
+    muca_params params;          /* either schedule, no resume                             */
 } muca_request;
 
 typedef struct {

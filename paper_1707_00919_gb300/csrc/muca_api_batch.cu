@@ -157,25 +157,62 @@ int build_graph(muca_batch_t b)
     return MUCA_OK;
 }
 
-int check_iteration_params(const muca_params &p, muca_t h)
+int check_iteration_params(const muca_params &p)
 {
-    if (p.schedule != MUCA_SCHEDULE_SWEEPS)
-        return fail(MUCA_EINVAL, "batched iteration supports the fixed-sweep schedule");
+    if (p.schedule != MUCA_SCHEDULE_SWEEPS && p.schedule != MUCA_SCHEDULE_PAPER)
+        return fail(MUCA_EINVAL, "unknown schedule %d", p.schedule);
     if (p.stop_rule < MUCA_STOP_MIN_MEAN || p.stop_rule > MUCA_STOP_CHEBYSHEV || p.max_iterations < 1)
         return fail(MUCA_EINVAL, "bad stop rule or max_iterations");
     if (p.resume != 0 && p.resume != 1)
         return fail(MUCA_EINVAL, "resume must be 0 or 1");
-    if (p.sweeps_per_iter * (uint64_t)h->N > 0xFFFFFFFFull / 256ull)
-        return fail(MUCA_EINVAL, "sweeps_per_iter too large for one recording launch");
-    if (h->t % (uint64_t)h->N != 0)
-        return fail(MUCA_EINVAL, "batched launches need every member at a sweep boundary");
+    return MUCA_OK;
+}
+
+// Attempts per walker of member h's next iteration under p, from the member's iteration
+// state, as muca_iterate_until_flat forms them (Sec. 3: N_therm = f_therm w with
+// w = max(w', 10); Eq. (7) until an iteration has started at the full width, growth by
+// `growth` after it).  full_after is the full-coverage flag the member keeps if the
+// iteration is not its last.
+void iteration_counts(muca_t h, const muca_params &p, uint64_t &n_therm, uint64_t &n_upd, bool &full_after)
+{
+    full_after = h->sched.full != 0;
+    if (p.schedule == MUCA_SCHEDULE_SWEEPS) {
+        n_therm = p.therm_sweeps * (uint64_t)h->N;
+        n_upd = p.sweeps_per_iter * (uint64_t)h->N;
+        return;
+    }
+    const int32_t w = std::max(h->sched.prev_width, 10);
+    n_therm = (uint64_t)(p.f_therm * (double)w);
+    if (full_after) {
+        n_upd = (uint64_t)std::floor(p.growth * (double)h->sched.upd_prev) + 1u;
+    } else {
+        const double walkers = (double)(h->total_walkers > 0 ? h->total_walkers : h->W);
+        n_upd = (uint64_t)std::floor(p.factor * std::pow((double)w, p.z) / walkers) + 1u;
+        full_after = h->sched.prev_width == h->N + 1;
+    }
+}
+
+// Reads the members' histograms and error words into their pinned buffers and waits.
+int read_back(muca_batch_t b, const std::vector<int32_t> &active)
+{
+    for (int32_t j : active) {
+        const muca_t h = b->inst[(size_t)j];
+        MUCA_CUDA(cudaMemcpyAsync(h->h_hist, h->d_hist, sizeof(unsigned long long) * ((size_t)h->N + 1),
+                                  cudaMemcpyDeviceToHost, b->stream),
+                  "histogram read");
+        MUCA_CUDA(cudaMemcpyAsync(h->h_err, h->d_err, sizeof(uint32_t), cudaMemcpyDeviceToHost, b->stream),
+                  "error word read");
+    }
+    MUCA_CUDA(cudaStreamSynchronize(b->stream), "batch synchronize");
     return MUCA_OK;
 }
 
 // One weight iteration of the members `active` (indices into b->inst): member j
-// thermalizes therm[j] sweeps and records rec[j] sweeps, all members in one replay of
-// the iteration graph.  Afterwards each member's histogram is in its pinned buffer and
-// its attempt counter is advanced.
+// thermalizes therm[j] attempts per walker and records rec[j], all members in one
+// replay of the iteration graph, or, when some member records more attempts than one
+// launch's 32-bit shared counts take, as a thermalization launch and several recording
+// launches issued directly.  Afterwards each member's histogram is in its pinned buffer
+// and its attempt counter is advanced.
 int batch_run_iteration(muca_batch_t b, const std::vector<int32_t> &active, const std::vector<uint64_t> &therm,
                         const std::vector<uint64_t> &rec)
 {
@@ -194,28 +231,79 @@ int batch_run_iteration(muca_batch_t b, const std::vector<int32_t> &active, cons
             return rc;
     }
     const size_t nm = active.size();
+    const uint64_t cap = max_recorded_attempts(256);
+    bool chunked = false;
+    for (size_t j = 0; j < nm; ++j)
+        chunked = chunked || rec[j] > cap;
     for (size_t j = 0; j < nm; ++j) {
         muca_t h = b->inst[(size_t)active[j]];
         build_table(h->L, h->lnW, h->h_table);
-        const uint64_t nt = therm[j] * (uint64_t)h->N, nr = rec[j] * (uint64_t)h->N;
-        b->h_args[j] = make_args(h, h->t, nt);
-        b->h_args[nm + j] = make_args(h, h->t + nt, nr);
-        h->t += nt + nr;
+        b->h_args[j] = make_args(h, h->t, therm[j]);
+        b->h_args[nm + j] = make_args(h, h->t + therm[j], std::min(rec[j], cap));
     }
-    MUCA_CUDA(cudaGraphLaunch(b->exec, b->stream), "batch iteration launch");
-    MUCA_CUDA(cudaStreamSynchronize(b->stream), "batch synchronize");
+    if (!chunked) {
+        MUCA_CUDA(cudaGraphLaunch(b->exec, b->stream), "batch iteration launch");
+        MUCA_CUDA(cudaStreamSynchronize(b->stream), "batch synchronize");
+    } else {
+        for (int32_t j : active) {
+            const muca_t h = b->inst[(size_t)j];
+            MUCA_CUDA(cudaMemcpyAsync(h->d_table, h->h_table, sizeof(uint32_t) * 5 * ((size_t)h->N + 1),
+                                      cudaMemcpyHostToDevice, b->stream),
+                      "table upload");
+        }
+        MUCA_CUDA(cudaMemcpyAsync(b->d_args, b->h_args, sizeof(muca::SweepArgs) * 2 * nm, cudaMemcpyHostToDevice,
+                                  b->stream),
+                  "batch descriptor upload");
+        MUCA_CUDA(cudaMemsetAsync(b->d_counter, 0, 2 * sizeof(uint32_t), b->stream), "work counter reset");
+        MUCA_CUDA(muca::launch_batch(b->d_args, b->d_items, b->n_items, b->d_counter, b->grid, b->smem, false,
+                                     b->stream),
+                  "batched thermalization");
+        for (int32_t j : active) {
+            const muca_t h = b->inst[(size_t)j];
+            MUCA_CUDA(cudaMemsetAsync(h->d_hist, 0, sizeof(unsigned long long) * ((size_t)h->N + 1), b->stream),
+                      "histogram reset");
+        }
+        for (uint64_t done = 0;;) {
+            MUCA_CUDA(muca::launch_batch(b->d_args + nm, b->d_items, b->n_items, b->d_counter + 1, b->grid, b->smem,
+                                         true, b->stream),
+                      "batched recording");
+            done += cap;
+            bool more = false;
+            for (size_t j = 0; j < nm; ++j)
+                more = more || rec[j] > done;
+            if (!more)
+                break;
+            // the next chunk: members that have finished record nothing
+            MUCA_CUDA(cudaStreamSynchronize(b->stream), "batch synchronize");
+            for (size_t j = 0; j < nm; ++j) {
+                const muca_t h = b->inst[(size_t)active[j]];
+                const uint64_t left = rec[j] > done ? rec[j] - done : 0u;
+                b->h_args[nm + j] = make_args(h, h->t + therm[j] + std::min(rec[j], done), std::min(left, cap));
+            }
+            MUCA_CUDA(cudaMemcpyAsync(b->d_args + nm, b->h_args + nm, sizeof(muca::SweepArgs) * nm,
+                                      cudaMemcpyHostToDevice, b->stream),
+                      "batch descriptor upload");
+            MUCA_CUDA(cudaMemsetAsync(b->d_counter + 1, 0, sizeof(uint32_t), b->stream), "work counter reset");
+        }
+        rc = read_back(b, active);
+        if (rc)
+            return rc;
+    }
+    for (size_t j = 0; j < nm; ++j)
+        b->inst[(size_t)active[j]]->t += therm[j] + rec[j];
     return check_members(b);
 }
 
 // Host half of one iteration for a member whose histogram is in its pinned buffer:
-// stop metric, flatness, Eq. (4) recursion.  Returns true when the member is finished
-// (flat, or max_iterations reached).
-bool member_update(muca_t h, const muca_params &p, muca_stats &s)
+// stop metric, flatness, Eq. (4) recursion and the member's iteration state (n_therm,
+// n_upd and full_after as iteration_counts gave them).  Returns true when the member is
+// finished (flat, or max_iterations reached).
+bool member_update(muca_t h, const muca_params &p, muca_stats &s, uint64_t n_therm, uint64_t n_upd, bool full_after)
 {
     const int32_t N = h->N;
     std::vector<uint64_t> H(h->h_hist, h->h_hist + N + 1);
     s.iterations += 1;
-    s.attempts_per_walker += (p.therm_sweeps + p.sweeps_per_iter) * (uint64_t)N;
+    s.attempts_per_walker += n_therm + n_upd;
     double metric;
     if (p.stop_rule == MUCA_STOP_MIN_MEAN)
         metric = min_over_mean(N, H);
@@ -237,7 +325,8 @@ bool member_update(muca_t h, const muca_params &p, muca_stats &s)
     h->sched.prev_lo = h->kl_lo;
     h->sched.prev_hi = h->kl_hi;
     h->sched.prev_width = h->kl_lo >= 0 ? h->kl_hi - h->kl_lo + 1 : 0;
-    h->sched.upd_prev = p.sweeps_per_iter * (uint64_t)N;
+    h->sched.full = full_after ? 1 : 0;
+    h->sched.upd_prev = n_upd;
     return s.iterations >= p.max_iterations;
 }
 
@@ -406,9 +495,6 @@ int muca_batch_sweep(muca_batch_t b, uint64_t n_sweeps, int record)
         return fail(MUCA_EINVAL, "NULL batch");
     if (n_sweeps == 0)
         return MUCA_OK;
-    for (muca_t h : b->inst)
-        if (h->t % (uint64_t)h->N != 0)
-            return fail(MUCA_EINVAL, "batched launches need every member at a sweep boundary");
     // every work item is one block: its 32-bit shared counts take 256 walkers x attempts
     uint64_t max_n = UINT64_MAX;
     for (muca_t h : b->inst)
@@ -462,33 +548,41 @@ int muca_batch_iterate(muca_batch_t b, const muca_params *p_in, muca_stats *stat
     else
         muca_default_params(&p);
     const size_t n = b->inst.size();
-    for (muca_t h : b->inst) {
-        int rc = check_iteration_params(p, h);
-        if (rc)
-            return rc;
-    }
+    int rc = check_iteration_params(p);
+    if (rc)
+        return rc;
     const auto start = std::chrono::steady_clock::now();
     std::vector<muca_stats> st(n);
     std::memset(st.data(), 0, sizeof(muca_stats) * n);
     for (muca_t h : b->inst) {
-        h->kl_lo = p.resume ? h->sched.prev_lo : -1;
-        h->kl_hi = p.resume ? h->sched.prev_hi : -1;
+        if (!p.resume)
+            h->sched = IterSchedule{};
+        h->kl_lo = h->sched.prev_lo;
+        h->kl_hi = h->sched.prev_hi;
     }
     std::vector<int32_t> active(n);
     for (size_t i = 0; i < n; ++i)
         active[i] = (int32_t)i;
     bool timed_out = false;
     while (!active.empty()) {
-        std::vector<uint64_t> therm(active.size(), p.therm_sweeps), rec(active.size(), p.sweeps_per_iter);
-        int rc = batch_run_iteration(b, active, therm, rec);
+        const size_t na = active.size();
+        std::vector<uint64_t> therm(na), rec(na);
+        std::vector<char> full(na);
+        for (size_t j = 0; j < na; ++j) {
+            bool f;
+            iteration_counts(b->inst[(size_t)active[j]], p, therm[j], rec[j], f);
+            full[j] = f;
+        }
+        rc = batch_run_iteration(b, active, therm, rec);
         if (rc)
             return rc;
         const double now = std::chrono::duration<double>(std::chrono::steady_clock::now() - start).count();
         std::vector<int32_t> next;
-        for (int32_t i : active) {
+        for (size_t j = 0; j < na; ++j) {
+            const int32_t i = active[j];
             muca_stats &s = st[(size_t)i];
             s.seconds = now;
-            if (!member_update(b->inst[(size_t)i], p, s))
+            if (!member_update(b->inst[(size_t)i], p, s, therm[j], rec[j], full[j] != 0))
                 next.push_back(i);
         }
         active.swap(next);
@@ -634,10 +728,8 @@ int muca_server_submit(muca_server_t s, const muca_request *r, int64_t *id)
         return fail(MUCA_EINVAL, "n_walkers out of range");
     if (r->layout == MUCA_LAYOUT_AUTO || r->walkers_per_block == MUCA_WPB_TUNE)
         return fail(MUCA_EINVAL, "requests take an explicit layout and block size (0 = default)");
-    if (r->params.schedule != MUCA_SCHEDULE_SWEEPS || r->params.max_iterations < 1 || r->params.resume ||
-        r->params.stop_rule < MUCA_STOP_MIN_MEAN || r->params.stop_rule > MUCA_STOP_CHEBYSHEV ||
-        r->params.sweeps_per_iter * (uint64_t)r->L * (uint64_t)r->L > 0xFFFFFFFFull / 256ull)
-        return fail(MUCA_EINVAL, "request parameters: fixed-sweep schedule, valid stop rule and sweeps");
+    if (check_iteration_params(r->params) != MUCA_OK || r->params.resume)
+        return fail(MUCA_EINVAL, "request parameters: a schedule, a stop rule, max_iterations >= 1, no resume");
     ServerRequest q;
     q.req = *r;
     q.t_arrival = server_now(s);
@@ -701,11 +793,13 @@ int muca_server_step(muca_server_t s, int32_t *n_active, int32_t *n_queued)
         const size_t na = s->active.size();
         std::vector<int32_t> members(na);
         std::vector<uint64_t> therm(na), rec(na);
+        std::vector<char> full(na);
         for (size_t j = 0; j < na; ++j) {
             const ServerRequest &q = s->reqs[(size_t)s->active[j]];
             members[j] = (int32_t)j;
-            therm[j] = q.req.params.therm_sweeps;
-            rec[j] = q.req.params.sweeps_per_iter;
+            bool f;
+            iteration_counts(q.h, q.req.params, therm[j], rec[j], f);
+            full[j] = f;
         }
         int rc = batch_run_iteration(s->batch, members, therm, rec);
         if (rc)
@@ -715,9 +809,9 @@ int muca_server_step(muca_server_t s, int32_t *n_active, int32_t *n_queued)
         std::vector<int64_t> next;
         for (size_t j = 0; j < na; ++j) {
             ServerRequest &q = s->reqs[(size_t)s->active[j]];
-            s->attempts += (therm[j] + rec[j]) * (uint64_t)q.h->N * (uint64_t)q.h->W;
+            s->attempts += (therm[j] + rec[j]) * (uint64_t)q.h->W;
             q.st.seconds = now - q.t_admit;
-            if (!member_update(q.h, q.req.params, q.st)) {
+            if (!member_update(q.h, q.req.params, q.st, therm[j], rec[j], full[j] != 0)) {
                 next.push_back(s->active[j]);
                 continue;
             }

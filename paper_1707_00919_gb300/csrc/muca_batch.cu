@@ -12,7 +12,8 @@ namespace {
 // Batched persistent kernel: one launch advances many instances (uneven L, walker
 // counts, tables and histograms).  The work list holds (instance, first walker, walker
 // count) items; each block takes the next item from a global counter, runs it with the
-// body of the whole-sweep kernel for that instance's L and layout, and takes another
+// body of the whole-sweep kernel for that instance's L and layout (with its partial-row
+// path where the instance's launch starts or ends inside a sweep), and takes another
 // until the list is exhausted.  The counter must be zero at launch.
 // ---------------------------------------------------------------------------------
 template <bool RECORD>
@@ -33,12 +34,12 @@ __global__ void __launch_bounds__(256, 1) batch_kernel(const SweepArgs *__restri
         const BatchItem it = items[k];
         const SweepArgs a = insts[it.inst];
         switch (a.L) {
-        case 8: batch_item<8, RECORD>(a, it, smem); break;
-        case 16: batch_item<16, RECORD>(a, it, smem); break;
-        case 24: batch_item<24, RECORD>(a, it, smem); break;
-        case 32: batch_item<32, RECORD>(a, it, smem); break;
-        case 48: batch_item<48, RECORD>(a, it, smem); break;
-        case 64: batch_item<64, RECORD, false, batch_table_stride(64)>(a, it, smem); break;
+        case 8: batch_item<8, RECORD, false, kTableStride, true>(a, it, smem); break;
+        case 16: batch_item<16, RECORD, false, kTableStride, true>(a, it, smem); break;
+        case 24: batch_item<24, RECORD, false, kTableStride, true>(a, it, smem); break;
+        case 32: batch_item<32, RECORD, false, kTableStride, true>(a, it, smem); break;
+        case 48: batch_item<48, RECORD, false, kTableStride, true>(a, it, smem); break;
+        case 64: batch_item<64, RECORD, false, batch_table_stride(64), true>(a, it, smem); break;
         default: break;
         }
     }

@@ -471,10 +471,14 @@ __device__ __forceinline__ void process_row(const uint32_t (&U)[L / 8], uint32_t
             C[x >> 3] ^= acc ? (1u << (4 * (x & 7))) : 0u;
             if (x == 0)
                 adj_last = acc ? adj_if_flip : 0u;
-            if (RECORD && in_range)
-                hist_add_one(Epost);
-            else
+            if (RECORD) {
+                // masked attempts of a recording launch count nothing (with 6-word rows
+                // there is no padding word to send them to)
+                if (in_range)
+                    hist_add_one(Epost);
+            } else {
                 pad_add_one<STRIDE>(Epost);
+            }
             // candidates of attempt x + 2 for both outcomes of attempt x + 1
             T0n = T0nn;
             T1n = T1nn;
@@ -853,11 +857,17 @@ __device__ __forceinline__ void sweep_block(const SweepArgs &a, int64_t wbase, i
         a.energy[w] = e;
 }
 
-// A batched work item: the whole-sweep body of the item's instance.
-template <int L, bool RECORD, bool GUARD = false, int STRIDE = kTableStride>
+// A batched work item: the whole-sweep body of the item's instance.  ANY_RANGE: the
+// item's launch may start or end inside a sweep (the Eq. (7) schedule's attempt
+// counts), which then takes the body with the partial-row path.
+template <int L, bool RECORD, bool GUARD = false, int STRIDE = kTableStride, bool ANY_RANGE = false>
 __device__ __forceinline__ void batch_item(const SweepArgs &a, const BatchItem &it, unsigned char *smem)
 {
-    sweep_block<L, RECORD, false, GUARD, STRIDE>(a, it.wbase, it.wpb, smem, a.layout);
+    constexpr uint64_t N = (uint64_t)L * (uint64_t)L;
+    if (!ANY_RANGE || (a.t0 % N == 0 && a.n % N == 0))
+        sweep_block<L, RECORD, false, GUARD, STRIDE>(a, it.wbase, it.wpb, smem, a.layout);
+    else
+        sweep_block<L, RECORD, true, GUARD, STRIDE>(a, it.wbase, it.wpb, smem, a.layout);
 }
 
 }  // namespace

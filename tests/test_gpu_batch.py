@@ -122,3 +122,57 @@ def test_config4_mix_sampled_walkers(M, orc):
         assert np.array_equal(lat[pick], s) and np.array_equal(e[pick], eo), (i, L, W)
     for m in inst:
         m.close()
+
+
+@pytest.mark.parametrize("stop_rule,threshold", [(0, 0.8), (1, 1e-4)])
+def test_batch_iterate_paper_schedule_equals_single(M, stop_rule, threshold):
+    """Eq. (7) schedule (Sec. 3) in the batched iteration: every member follows its own
+    visited ranges, its thermalization and recording launches start and end inside
+    sweeps, and each member's iteration count, stop metric, weights, energies and
+    attempt counter equal the instance iterated alone."""
+    specs = [(8, 128, 11), (16, 256, 12), (8, 64, 13), (24, 512, 14), (16, 1024, 15)]
+    if stop_rule == 0:   # the 6-word table rows of L = 64 items and L = 48 as well
+        specs += [(64, 1024, 16), (48, 256, 17), (32, 256, 18)]
+    p = M.make_params(schedule=M.MUCA_SCHEDULE_PAPER, stop_rule=stop_rule, flat_threshold=threshold,
+                      max_iterations=400)
+    alone = []
+    for L, W, seed in specs:
+        with M.Muca(L, W, seed) as m:
+            st = m.iterate_until_flat(p)
+            alone.append((st, m.get_weights(), m.get_energies(), m.attempt_counter))
+    inst = [M.Muca(L, W, seed) for L, W, seed in specs]
+    with M.Batch(inst) as b:
+        rc, stats = b.iterate_until_flat(p)
+    for i, m in enumerate(inst):
+        st, lnW, e, t = alone[i]
+        assert t % (specs[i][0] ** 2) != 0 or st.iterations > 0
+        assert stats[i].iterations == st.iterations and stats[i].converged == st.converged, i
+        assert stats[i].last_metric == st.last_metric
+        assert stats[i].attempts_per_walker == st.attempts_per_walker
+        assert np.array_equal(m.get_weights(), lnW)
+        assert np.array_equal(m.get_energies(), e)
+        assert m.attempt_counter == t
+        m.close()
+
+
+def test_batch_iteration_longer_than_one_recording_launch(M):
+    """Members that record more than 0xFFFFFFFF / 256 attempts per walker in one
+    iteration (the 32-bit per-block counts of one launch) run several recording launches
+    per iteration, of different lengths for members whose counts end at different
+    points; each member equals its instance iterated alone."""
+    specs = [(8, 32, 21), (8, 64, 22)]
+    p = M.make_params(therm_sweeps=31, sweeps_per_iter=262_200, max_iterations=2)
+    alone = []
+    for L, W, seed in specs:
+        with M.Muca(L, W, seed) as m:
+            st = m.iterate_until_flat(p)
+            alone.append((st, m.get_weights(), m.get_energies(), m.get_lattice(), m.attempt_counter))
+    inst = [M.Muca(L, W, seed) for L, W, seed in specs]
+    with M.Batch(inst) as b:
+        rc, stats = b.iterate_until_flat(p)
+    for i, m in enumerate(inst):
+        st, lnW, e, lat, t = alone[i]
+        assert stats[i].iterations == st.iterations and stats[i].last_metric == st.last_metric
+        assert np.array_equal(m.get_weights(), lnW) and np.array_equal(m.get_lattice(), lat)
+        assert np.array_equal(m.get_energies(), e) and m.attempt_counter == t
+        m.close()

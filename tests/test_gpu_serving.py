@@ -80,6 +80,35 @@ def test_requests_alone_and_in_the_mix_agree(M, orc):
             assert np.array_equal(srv.weights(rid, L * L + 1), lnW), (L, W)
 
 
+def test_paper_schedule_requests_alone_and_in_the_mix(M):
+    """Requests with the Eq. (7) schedule (each member grows its own update counts) are
+    served together and each equals the same request run alone, bit for bit."""
+    specs = [(8, 64, 31), (16, 256, 32), (24, 512, 33), (8, 128, 34)]
+    p = M.make_params(schedule=M.MUCA_SCHEDULE_PAPER, stop_rule=M.MUCA_STOP_MIN_MEAN, flat_threshold=0.8,
+                      max_iterations=500)
+    alone = []
+    for L, W, seed in specs:
+        with M.Muca(L, W, seed) as m:
+            st = m.iterate_until_flat(p)
+            alone.append((st, m.get_weights()))
+    with M.Server(1 << 30) as srv:
+        ids = [srv.submit(L, W, seed, p) for L, W, seed in specs[:2]]
+        active, _ = srv.step()
+        ids += [srv.submit(L, W, seed, p) for L, W, seed in specs[2:]]   # arrive while others run
+        for _ in range(5000):
+            active, queued = srv.step()
+            if active == 0 and queued == 0:
+                break
+        for k, rid in enumerate(ids):
+            L, W, seed = specs[k]
+            st = srv.status(rid)
+            ref, lnW = alone[k]
+            assert st.state == M.C.MUCA_REQ_DONE and st.stats.converged == ref.converged
+            assert st.stats.iterations == ref.iterations and st.stats.last_metric == ref.last_metric
+            assert st.stats.attempts_per_walker == ref.attempts_per_walker
+            assert np.array_equal(srv.weights(rid, L * L + 1), lnW)
+
+
 def test_server_rejects_bad_requests(M):
     with M.Server(1 << 20) as srv:
         with pytest.raises(M.MucaError):
