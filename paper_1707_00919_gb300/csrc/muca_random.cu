@@ -195,6 +195,7 @@ __global__ void __launch_bounds__(256) random_sweep_kernel(const SweepArgs a)
     auto row = [&](uint32_t off) { return *reinterpret_cast<const RowT *>(cbytes + off); };
     const uint32_t k0 = (uint32_t)a.seed, k1 = (uint32_t)(a.seed >> 32);
     const uint32_t wid = a.walker0 + (uint32_t)w;
+    const PhiloxKeys pk = make_keys(a.seed, wid, (uint32_t)(a.t0 >> 34));
     const uint64_t tend = a.t0 + a.n;
     const uint32_t rb = (uint32_t)wpb * (uint32_t)sizeof(RowT);   // bytes between rows of a column
     for (uint64_t tc = a.t0; tc < tend; tc += kChunk) {
@@ -266,8 +267,10 @@ __global__ void __launch_bounds__(256) random_sweep_kernel(const SweepArgs a)
                 hist_count(E);
         };
         auto words = [&](uint64_t tt) {
-            const uint64_t blk = tt >> 2;
-            const uint4 q = philox4x32_10(make_uint4((uint32_t)blk, (uint32_t)(blk >> 32), wid, kTagMetropolis), k0, k1);
+            // the walker's stream of typewriter order (tag 0) with the keys and the products
+            // that depend only on the walker and counter word 1 computed once (the launch
+            // keeps t >> 34 fixed)
+            const uint4 q = philox_walker_c1((uint32_t)(tt >> 2), pk);
             // clamped so that "r < T" also accepts every attempt when T = 0xFFFFFFFF
             return make_uint4(min(q.x, 0xFFFFFFFEu), min(q.y, 0xFFFFFFFEu), min(q.z, 0xFFFFFFFEu),
                               min(q.w, 0xFFFFFFFEu));
@@ -432,6 +435,17 @@ cudaError_t launch_random_sweep(const SweepArgs &a, int walkers_per_block, bool 
         wpb -= 32;
     if (random_smem_bytes(a.L, wpb, record) > limit)
         return cudaErrorInvalidConfiguration;
+    // the kernel keeps Philox counter word 1 (t >> 34) fixed within a launch: a range that
+    // crosses a multiple of 2^34 runs as two launches
+    const uint64_t step = a.t0 >> 34;
+    if (((a.t0 + a.n - 1) >> 34) != step) {
+        SweepArgs first = a, second = a;
+        first.n = ((step + 1) << 34) - a.t0;
+        second.t0 = a.t0 + first.n;
+        second.n = a.n - first.n;
+        cudaError_t err = launch_random_sweep(first, walkers_per_block, record, s);
+        return err != cudaSuccess ? err : launch_random_sweep(second, walkers_per_block, record, s);
+    }
     if (a.L <= 32)
         return launch_random_row<uint32_t>(a, wpb, record, s);
     return launch_random_row<unsigned long long>(a, wpb, record, s);

@@ -134,3 +134,30 @@ def test_full_size_sampled_walkers(muca_mod, orc):
         orc.run(L, seed, s, eo, T, 0, 3 * N, False, walker0=w, site_order=1)
         orc.run(L, seed, s, eo, T, 3 * N, 2 * N, True, walker0=w, site_order=1)
         assert np.array_equal(lat[w], s[0]) and e[w] == eo[0], w
+
+
+@pytest.mark.parametrize("L", [8, 32, 64])
+def test_counter_high_word_boundary(muca_mod, orc, L):
+    """Attempt counters around t = 2^34, where Philox counter word 1 (t >> 34) steps: a
+    launch across the step (run as two launches) and launches after it equal the oracle
+    in random order (the kernel takes round 1's product of the acceptance stream from
+    its keys, valid while word 1 stays at the launch's first value)."""
+    M = muca_mod
+    N = L * L
+    W = 40
+    lnW = rand_weights(L, 3, 0.3)
+    t0 = 2**34 - 2 * N - 5
+    with M.Muca(L, W, 19) as m:
+        m.site_order = M.MUCA_ORDER_RANDOM
+        m.set_weights(lnW)
+        m.set_attempt_counter(t0)
+        m.reset_histogram()
+        m.attempts(4 * N + 9, True)
+        m.attempts(N, False)
+        lat, e, H, t = m.get_lattice(), m.get_energies(), m.get_histogram(), m.attempt_counter
+    s, eo = orc.init(L, 19, W)
+    T = orc.build_table(L, lnW)
+    Ho = orc.run(L, 19, s, eo, T, t0, 4 * N + 9, True, site_order=1)
+    orc.run(L, 19, s, eo, T, t0 + 4 * N + 9, N, False, site_order=1)
+    assert t == t0 + 5 * N + 9
+    assert np.array_equal(lat, s) and np.array_equal(e, eo) and np.array_equal(H, Ho)
