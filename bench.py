@@ -549,15 +549,18 @@ def run_native(args):
     mr.site_order = M.MUCA_ORDER_RANDOM
     mr.set_weights(perfect_weights(L_SIDE))
     mr.sweep(3, record=False)
-    rnd_s = time_recorded_sweeps(mr, stream, 2, 5)
+    rnd_s = time_recorded_sweeps(mr, stream, SWEEPS_PER_ITER, 5)
     mr.close()
-    rnd_rate = WALKERS * 2 * N / rnd_s
+    rnd_rate = WALKERS * SWEEPS_PER_ITER * N / rnd_s
     result["paper_protocol"] = {"attempts_per_s": pp_rate, "ns_per_flip": 1e9 / pp_rate,
                                 "protocol": f"ln W = -ln g exact, {THERM_SWEEPS} sweeps to equilibrate, "
                                             f"median of 7 launches of {SWEEPS_PER_ITER} recorded sweeps"}
     result["random_site_order"] = {"attempts_per_s": rnd_rate, "ns_per_flip": 1e9 / rnd_rate,
-                                   "protocol": "perfect weights, 3 sweeps to equilibrate, median of 5 launches "
-                                               "of 2 recorded sweeps in random shared site order"}
+                                   # the same integer-issue roofline as the typewriter kernel
+                                   "roofline_frac": OPS_PER_ATTEMPT * rnd_rate / 1e12 / peak_tops,
+                                   "typewriter_roofline_frac": achieved_tops / peak_tops,
+                                   "protocol": f"perfect weights, 3 sweeps to equilibrate, median of 5 launches "
+                                               f"of {SWEEPS_PER_ITER} recorded sweeps in random shared site order"}
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:   # the oracle baseline at N = 1 only
         rate, cores, wall = cpu_baseline(lnW, WALKERS)
         result["cpu_baseline"] = {"value": rate, "unit": "attempts/s", "cores": cores, "kind": "oracle",
