@@ -121,3 +121,25 @@ def test_reference_arm_json_line():
     assert d["cpu_baseline"]["value"] == d["value"] and d["cpu_baseline"]["sample"]
     assert d["e2e"] == {"value": d["value"], "unit": "attempts/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}
     assert d["config"]["L"] == 32 and d["config"]["walkers"] == 16384
+
+
+def test_cpu_time_to_flat_is_the_oracle_iteration(orc):
+    """The benchmark's CPU time-to-flat (walkers sharded over host processes, histograms
+    summed, the oracle's flatness test and Eq. (4) recursion on the host) runs exactly
+    the oracle's own weight iteration: the same iteration count and the same final
+    weights bit for bit (here L = 8, 128 walkers, 31 + 100 sweeps per iteration)."""
+    import numpy as np
+    import bench
+    saved = (bench.L_SIDE, bench.WALKERS, bench.SWEEPS_PER_ITER)
+    try:
+        bench.L_SIDE, bench.WALKERS, bench.SWEEPS_PER_ITER = 8, 128, 100
+        secs, its, conv, lnW, procs = bench.cpu_time_to_flat(128, cores=3, max_iterations=200)
+    finally:
+        bench.L_SIDE, bench.WALKERS, bench.SWEEPS_PER_ITER = saved
+    s, e = orc.init(8, bench.SEED, 128)
+    ref = np.zeros(65)
+    p = orc.make_params(schedule=0, stop_rule=0, flat_threshold=0.8, therm_sweeps=bench.THERM_SWEEPS,
+                        sweeps_per_iter=100, max_iterations=200)
+    res, _, _, _ = orc.iterate(8, bench.SEED, s, e, ref, 0, p)
+    assert conv and res.converged == 1 and its == res.iterations and procs == 3
+    assert np.array_equal(lnW, ref)
