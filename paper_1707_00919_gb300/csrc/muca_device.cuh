@@ -636,6 +636,41 @@ struct AttemptStream {
 
 // nsweeps whole sweeps of one walker from Philox block blk (column 0 of row 0); U, C, D
 // hold rows L - 1, 0 and 1 on entry and are left in the same state on exit.
+// nrows whole rows of one walker as one continuous attempt stream, from row y0 (wrapping
+// to row 0 after row L - 1) whose column 0 lies in Philox block blk; U, C, D hold rows
+// y0 - 1, y0 and y0 + 1 on entry and the rows around the next row on exit.  Counter
+// word 1 must stay at pk.c1 for the whole range.
+template <int L, bool RECORD, int STRIDE>
+__device__ __forceinline__ void stream_rows_c1(const SmemRows<L> &rows, uint32_t (&U)[L / 8], uint32_t (&C)[L / 8],
+                                               uint32_t (&D)[L / 8], uint32_t &E, uint64_t blk, int y0,
+                                               uint64_t nrows, const PhiloxKeys &pk)
+{
+    constexpr int NW = L / 8;
+    uint32_t b = (uint32_t)blk;
+    uint4 carry = PhiloxSourceC1<L>::words(b, pk);
+    AttemptStream<L, STRIDE> st;
+    st.start(U, C, D, E);
+    int y = y0;
+#pragma unroll 1
+    for (uint64_t r = 0; r < nrows; ++r) {
+        const int y2 = (y + 2 < L) ? y + 2 : y + 2 - L;
+        uint32_t D2[NW];
+        rows.load(y2, D2);
+        const PhiloxSourceC1<L> src{b, &pk, &carry};
+        st.template row<RECORD>(U, C, D, D2, src);
+        rows.store(y, C);
+#pragma unroll
+        for (int i = 0; i < NW; ++i) {
+            U[i] = C[i];
+            C[i] = D[i];
+            D[i] = D2[i];
+        }
+        b += (uint32_t)(L / 4);
+        y = (y + 1 == L) ? 0 : y + 1;
+    }
+    E = st.E;
+}
+
 // Counter word 1 must stay at pk.c1 for the whole range.  The row below the next one is
 // loaded from shared memory when a row starts (the current row does not change it), and
 // the next row's first Philox block is computed during the current row.
@@ -644,30 +679,7 @@ __device__ __forceinline__ void whole_sweeps_c1(const SmemRows<L> &rows, uint32_
                                                 uint32_t (&D)[L / 8], uint32_t &E, uint64_t blk, uint64_t nsweeps,
                                                 const PhiloxKeys &pk)
 {
-    constexpr int NW = L / 8;
-    uint32_t b = (uint32_t)blk;
-    uint4 carry = PhiloxSourceC1<L>::words(b, pk);
-    AttemptStream<L, STRIDE> st;
-    st.start(U, C, D, E);
-    for (uint64_t s = 0; s < nsweeps; ++s) {
-#pragma unroll 1
-        for (int y = 0; y < L; ++y) {
-            const int y2 = (y + 2 < L) ? y + 2 : y + 2 - L;
-            uint32_t D2[NW];
-            rows.load(y2, D2);
-            const PhiloxSourceC1<L> src{b, &pk, &carry};
-            st.template row<RECORD>(U, C, D, D2, src);
-            rows.store(y, C);
-#pragma unroll
-            for (int i = 0; i < NW; ++i) {
-                U[i] = C[i];
-                C[i] = D[i];
-                D[i] = D2[i];
-            }
-            b += (uint32_t)(L / 4);
-        }
-    }
-    E = st.E;
+    stream_rows_c1<L, RECORD, STRIDE>(rows, U, C, D, E, blk, 0, nsweeps * (uint64_t)L, pk);
 }
 
 // The same with the general generator (any counter range).
@@ -791,39 +803,65 @@ __device__ __forceinline__ void sweep_block(const SweepArgs &a, int64_t wbase, i
             else
                 whole_sweeps<L, RECORD, STRIDE>(rows, U, C, D, E, a.t0 >> 2, a.n / (uint64_t)N, pk);
         } else {
-            // any attempt range: rows cut by the launch's start or end run masked
+            // any attempt range: a first row cut by the launch's start and a last row cut
+            // by its end run masked, the whole rows between them as one attempt stream
             uint64_t t = a.t0;
             const uint64_t tend = a.t0 + a.n;
             int y = (int)((t % (uint64_t)N) / L);
-            int x0 = (int)((t % (uint64_t)N) % L);
+            const int x0 = (int)((t % (uint64_t)N) % L);
             uint64_t blk = (t - (uint64_t)x0) >> 2;   // Philox block of column 0 of row y
             rows.load((y + L - 1) % L, U);
             rows.load(y, C);
             rows.load((y + 1) % L, D);
-            while (t < tend) {
+            bool ended = false;
+            if (x0 != 0 || tend - t < (uint64_t)L) {
                 const uint64_t left = tend - t;
+                const int xe = left < (uint64_t)(L - x0) ? x0 + (int)left : L;
                 const PhiloxSource src{blk, &pk};
-                int xe = L;
-                if (x0 == 0 && left >= (uint64_t)L) {
-                    process_row<L, RECORD, false, PhiloxSource, STRIDE>(U, C, D, E, src);
-                } else {
-                    xe = left < (uint64_t)(L - x0) ? x0 + (int)left : L;
-                    process_row<L, RECORD, true, PhiloxSource, STRIDE>(U, C, D, E, src, x0, xe);
-                }
+                process_row<L, RECORD, true, PhiloxSource, STRIDE>(U, C, D, E, src, x0, xe);
                 rows.store(y, C);
                 t += (uint64_t)(xe - x0);
-                if (xe < L)
-                    break;   // the launch ends inside this row
-                const int y2 = (y + 2 < L) ? y + 2 : y + 2 - L;
+                ended = xe < L;   // the launch ends inside this row
+                if (!ended) {
+                    const int y2 = (y + 2 < L) ? y + 2 : y + 2 - L;
 #pragma unroll
-                for (int i = 0; i < NW; ++i) {
-                    U[i] = C[i];
-                    C[i] = D[i];
+                    for (int i = 0; i < NW; ++i) {
+                        U[i] = C[i];
+                        C[i] = D[i];
+                    }
+                    rows.load(y2, D);
+                    y = (y + 1 == L) ? 0 : y + 1;
+                    blk += (uint64_t)(L / 4);
                 }
-                rows.load(y2, D);
-                y = (y + 1 == L) ? 0 : y + 1;
-                x0 = 0;
-                blk += (uint64_t)(L / 4);
+            }
+            const uint64_t nwhole = ended ? 0u : (tend - t) / (uint64_t)L;
+            if (nwhole > 0) {
+                if (C1_ONLY || (a.t0 >> 34) == ((a.t0 + a.n - 1) >> 34)) {
+                    stream_rows_c1<L, RECORD, STRIDE>(rows, U, C, D, E, blk, y, nwhole, pk);
+                } else {
+#pragma unroll 1
+                    for (uint64_t r = 0; r < nwhole; ++r) {
+                        const PhiloxSource src{blk + r * (uint64_t)(L / 4), &pk};
+                        const int yr = (int)(((uint64_t)y + r) % (uint64_t)L);
+                        process_row<L, RECORD, false, PhiloxSource, STRIDE>(U, C, D, E, src);
+                        rows.store(yr, C);
+                        const int y2 = (yr + 2 < L) ? yr + 2 : yr + 2 - L;
+#pragma unroll
+                        for (int i = 0; i < NW; ++i) {
+                            U[i] = C[i];
+                            C[i] = D[i];
+                        }
+                        rows.load(y2, D);
+                    }
+                }
+                t += nwhole * (uint64_t)L;
+                y = (int)(((uint64_t)y + nwhole) % (uint64_t)L);
+                blk += nwhole * (uint64_t)(L / 4);
+            }
+            if (!ended && t < tend) {   // the launch ends inside the next row
+                const PhiloxSource src{blk, &pk};
+                process_row<L, RECORD, true, PhiloxSource, STRIDE>(U, C, D, E, src, 0, (int)(tend - t));
+                rows.store(y, C);
             }
         }
         e = (int32_t)((E - tbase) / (4u * STRIDE));
