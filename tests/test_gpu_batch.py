@@ -176,3 +176,30 @@ def test_batch_iteration_longer_than_one_recording_launch(M):
         assert np.array_equal(m.get_weights(), lnW) and np.array_equal(m.get_lattice(), lat)
         assert np.array_equal(m.get_energies(), e) and m.attempt_counter == t
         m.close()
+
+
+def test_batch_sweep_from_inside_a_sweep(M, orc):
+    """Members whose attempt counters lie inside a sweep (after partial launches of their
+    own): a batched launch of whole sweeps then starts and ends inside a row for them, and
+    every member equals the oracle."""
+    specs = [(8, 40, 0, 5), (32, 70, 1, 1024 + 37), (64, 33, 0, 13), (24, 50, 1, 0)]
+    inst = []
+    for i, (L, W, lay, head) in enumerate(specs):
+        m = M.Muca(L, W, 300 + i, layout=lay)
+        m.set_weights(weights(L, 60 + i))
+        if head:
+            m.attempts(head, False)
+        m.reset_histogram()
+        inst.append(m)
+    with M.Batch(inst) as b:
+        b.sweep(2, record=True)
+        res = [(m.get_lattice(), m.get_energies(), m.get_histogram(), m.attempt_counter) for m in inst]
+    for i, (L, W, lay, head) in enumerate(specs):
+        N = L * L
+        plan = ([(head, False)] if head else []) + [(2 * N, True)]
+        s, e, H = oracle_advance(orc, L, W, 300 + i, weights(L, 60 + i), plan)
+        lat, ed, Hd, t = res[i]
+        assert t == head + 2 * N
+        assert np.array_equal(lat, s) and np.array_equal(ed, e) and np.array_equal(Hd, H), (L, W, lay)
+    for m in inst:
+        m.close()
