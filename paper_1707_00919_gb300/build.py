@@ -12,9 +12,9 @@ ROOT = os.path.dirname(PKG)
 CSRC = os.path.join(PKG, "csrc")
 BUILD = os.path.join(PKG, "_build")
 LIB = os.path.join(PKG, "libmuca.so")
-SOURCES = ["muca_kernels.cu", "muca_batch.cu", "muca_noalloc.cu", "muca_iterate.cu", "muca_random.cu", "muca_probe.cu", "muca_api.cu",
+SOURCES = ["muca_batch_rec.cu", "muca_batch.cu", "muca_noalloc.cu", "muca_kernels.cu", "muca_iterate.cu", "muca_random.cu", "muca_probe.cu", "muca_api.cu",
            "muca_api_iterate.cu", "muca_api_batch.cu"] + [f"muca_full_{L}.cu" for L in (8, 16, 24, 32, 48, 64)]
-HEADERS = ["muca_internal.h", "muca_device.cuh", "muca_full.cuh", "muca_math.cuh", "muca_host.h"]
+HEADERS = ["muca_internal.h", "muca_device.cuh", "muca_full.cuh", "muca_batch.cuh", "muca_math.cuh", "muca_host.h"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 

@@ -141,6 +141,11 @@ cudaError_t configure_batch(size_t smem);
 int batch_resident_blocks(size_t smem);
 cudaError_t launch_batch(const SweepArgs *insts, const BatchItem *items, int32_t n_items, uint32_t *counter,
                          int grid, size_t smem, bool record, cudaStream_t s);
+// The recording instantiation of the batched kernel (its own translation unit).
+cudaError_t configure_batch_record(size_t smem);
+int batch_resident_blocks_record(size_t smem);
+cudaError_t launch_batch_record(const SweepArgs *insts, const BatchItem *items, int32_t n_items, uint32_t *counter,
+                                int grid, size_t smem, cudaStream_t s);
 
 // Allocation-free batched sweep (see muca_batch_sweep_noalloc in muca.h): descriptors,
 // walkers per item and the prefix sums of the work items per instance (prefix[0] = 0,
