@@ -13,8 +13,9 @@ Reported:
   time_to_flat wall time of muca_iterate_until_flat from ln W = 0 until min/mean >= 0.8;
   e2e          the same steps through the C ABI with host weights in and the host
                histogram out (copies inside the timed region), host wall clock;
-  roofline     the recorded-sweep kernel against the integer-issue ceiling (and against
-               the measured issue rate of a balanced integer mix);
+  roofline     the step's sweep kernel (one launch: 31 thermalization sweeps, then 10
+               recorded sweeps) against the integer-issue ceiling (and against the
+               measured issue rate of a balanced integer mix);
   cpu_baseline the C oracle on the host cores: one step of the same workload on all cores
                and on one thread, and its whole weight iteration to a flat histogram.
 
@@ -80,13 +81,17 @@ def perfect_weights(L: int):
     return np.where(np.isfinite(lng), -lng, 0.0)
 
 
-def time_recorded_sweeps(m, stream, sweeps: int, reps: int) -> float:
-    """Median device time (s) of `sweeps` recorded sweeps on the instance's stream."""
+def time_recorded_sweeps(m, stream, sweeps: int, reps: int, lead: int = 0) -> float:
+    """Median device time (s) of a launch of `sweeps` recorded sweeps on the instance's
+    stream; lead > 0 queues that many thermalization sweeps before each timed launch, so
+    that the GPU is busy while the host enqueues it (the window then holds no host time)."""
     import torch
     ts = []
     for _ in range(reps):
         a = torch.cuda.Event(enable_timing=True)
         b = torch.cuda.Event(enable_timing=True)
+        if lead:
+            m.sweep(lead, record=False)
         a.record(stream)
         m.sweep(sweeps, record=True)
         b.record(stream)
@@ -207,8 +212,9 @@ def kernel_source_hash() -> str:
 
 
 def profiled_traffic():
-    """DRAM bytes (read + write) per recorded-sweep launch from the committed ncu
-    summary, or None when the kernel source changed since that capture."""
+    """DRAM bytes (read + write) per launch of the step's sweep kernel (thermalization and
+    recorded sweeps) from the committed ncu summary, or None when the kernel source
+    changed since that capture."""
     try:
         text = open(TRAFFIC_PROFILE).read()
     except OSError:
@@ -221,7 +227,7 @@ def profiled_traffic():
     if vals.get("kernel_source_sha256_16") != kernel_source_hash():
         return None
     try:
-        return float(vals["dram_bytes_per_record_launch"])
+        return float(vals["dram_bytes_per_step_launch"])
     except (KeyError, ValueError):
         return None
 
@@ -403,19 +409,18 @@ def run_native(args):
     flat = [False]
 
     def step(ev=None):
-        """One weight iteration through the C ABI (table build and upload, thermalization,
-        zeroed histogram, recorded sweeps, histogram read, the min/mean flatness test and
-        the Eq. (4) recursion, muca_flatness and muca_update_weights); ev = four CUDA
-        events on the instance's stream: step start, before the recorded sweeps, after
-        them, and after the host recursion (so a step's time includes the host work)."""
+        """One weight iteration through the C ABI (table build and upload; zeroed
+        histogram, thermalization and recorded sweeps in one muca_thermalize_and_record
+        call, one kernel launch; histogram read; the min/mean flatness test and the
+        Eq. (4) recursion, muca_flatness and muca_update_weights); ev = four CUDA events
+        on the instance's stream: step start, before the sampling call, after it, and
+        after the host recursion (so a step's time includes the host work)."""
         if ev:
             ev[0].record(stream)
         m.set_weights(lnW)
-        m.sweep(THERM_SWEEPS, record=False)
-        m.reset_histogram()
         if ev:
             ev[1].record(stream)
-        m.sweep(SWEEPS_PER_ITER, record=True)
+        m.thermalize_and_record(THERM_SWEEPS * N, SWEEPS_PER_ITER * N)
         if ev:
             ev[2].record(stream)
         H = m.get_histogram()
@@ -447,8 +452,8 @@ def run_native(args):
     t_timed1 = time.perf_counter()
     torch.cuda.nvtx.range_pop()
     step_ms = [evs[k][0].elapsed_time(evs[k][3]) for k in range(args.steps)]
-    therm_ms = [evs[k][0].elapsed_time(evs[k][1]) for k in range(args.steps)]
-    rec_ms = [evs[k][1].elapsed_time(evs[k][2]) for k in range(args.steps)]
+    table_ms = [evs[k][0].elapsed_time(evs[k][1]) for k in range(args.steps)]
+    sample_ms = [evs[k][1].elapsed_time(evs[k][2]) for k in range(args.steps)]
     total_s = sum(step_ms) / 1e3
     total_s = max_over_ranks(dist, total_s)
     barrier(dist)
@@ -473,9 +478,11 @@ def run_native(args):
     sm_max_mhz = float(peaks.get("sm_max_mhz", 2070.0))
     # integer-issue ceiling: every SM sub-partition issues one 32-lane instruction per clock
     peak_tops = sm_count * 4 * 32 * sm_max_mhz * 1e6 / 1e12
-    rec_launch_s = (sum(rec_ms) / len(rec_ms)) / 1e3
-    rec_attempts = WALKERS * SWEEPS_PER_ITER * N
-    achieved_tops = OPS_PER_ATTEMPT * rec_attempts / rec_launch_s / 1e12
+    # the sampling window holds the launch and the histogram zeroing before it (an 8 KB
+    # memset), which is counted against the kernel
+    launch_s = (sum(sample_ms) / len(sample_ms)) / 1e3
+    launch_attempts = WALKERS * (THERM_SWEEPS + SWEEPS_PER_ITER) * N
+    achieved_tops = OPS_PER_ATTEMPT * launch_attempts / launch_s / 1e12
     traffic = profiled_traffic()
     lattice_bytes = 2 * WALKERS * N   # int8 lattices read and written once per launch
     # measured issue rates of the instruction classes the sweep uses (context for the peak)
@@ -510,14 +517,15 @@ def run_native(args):
         "device_iteration_identical": bool(same_weights and st_dev.iterations == st.iterations),
         "flat": bool(st.converged),
         "flat_metric": st.last_metric,
-        "therm_ms_per_step": sum(therm_ms) / len(therm_ms),
-        "record_ms_per_step": sum(rec_ms) / len(rec_ms),
+        "table_ms_per_step": sum(table_ms) / len(table_ms),
+        "sweep_launch_ms_per_step": sum(sample_ms) / len(sample_ms),
         "e2e": {"value": e2e_value, "unit": "attempts/s",
                 "h2d_bytes_per_step": (N + 1) * 5 * 4, "d2h_bytes_per_step": (N + 1) * 8 + 4},
-        "gpu_launches": 2 * args.steps,
+        "gpu_launches": args.steps,
         "roofline": {"bound": "alu", "achieved": achieved_tops, "peak": peak_tops, "unit": "Tops/s (int32)",
                      "frac": achieved_tops / peak_tops, "traffic": traffic,
-                     "kernel": "sweep_full_kernel<32,int8,record>",
+                     "kernel": "sweep_full_kernel<32,int8,record> (31 thermalization + 10 recorded "
+                               "sweeps in one launch)",
                      "ops_per_attempt": OPS_PER_ATTEMPT,
                      "peak_basis": f"{sm_count} SMs x 4 issue slots x 32 lanes x {sm_max_mhz:.0f} MHz",
                      "measured_issue_tops": {k: round(v, 3) for k, v in probe.items()},
@@ -528,10 +536,10 @@ def run_native(args):
                      "single_warp_issue_frac": one_warp_frac,
                      "measured_philox_words_per_s": philox_words,
                      # lattice traffic of the same launch against HBM (not the bound)
-                     "hbm": {"algorithmic_bytes": lattice_bytes, "algorithmic_gbs": lattice_bytes / rec_launch_s / 1e9,
-                             "dram_gbs": (traffic / rec_launch_s / 1e9) if traffic else None,
+                     "hbm": {"algorithmic_bytes": lattice_bytes, "algorithmic_gbs": lattice_bytes / launch_s / 1e9,
+                             "dram_gbs": (traffic / launch_s / 1e9) if traffic else None,
                              "peak_gbs": peaks.get("hbm_gbs"),
-                             "frac": (lattice_bytes / rec_launch_s / 1e9 / peaks["hbm_gbs"])
+                             "frac": (lattice_bytes / launch_s / 1e9 / peaks["hbm_gbs"])
                              if peaks.get("hbm_gbs") else None}},
         "clocks": clock_summary,
     }
@@ -541,7 +549,7 @@ def run_native(args):
     mp_ = M.Muca(L_SIDE, WALKERS, seed, layout=M.MUCA_LAYOUT_INT8, stream=stream)
     mp_.set_weights(perfect_weights(L_SIDE))
     mp_.sweep(THERM_SWEEPS, record=False)
-    pp_s = time_recorded_sweeps(mp_, stream, SWEEPS_PER_ITER, 7)
+    pp_s = time_recorded_sweeps(mp_, stream, SWEEPS_PER_ITER, 7, lead=3)
     mp_.close()
     pp_rate = WALKERS * SWEEPS_PER_ITER * N / pp_s
     # the paper's random shared site order (Sec. 2.3) on the same workload
@@ -554,7 +562,13 @@ def run_native(args):
     rnd_rate = WALKERS * SWEEPS_PER_ITER * N / rnd_s
     result["paper_protocol"] = {"attempts_per_s": pp_rate, "ns_per_flip": 1e9 / pp_rate,
                                 "protocol": f"ln W = -ln g exact, {THERM_SWEEPS} sweeps to equilibrate, "
-                                            f"median of 7 launches of {SWEEPS_PER_ITER} recorded sweeps"}
+                                            f"median of 7 launches of {SWEEPS_PER_ITER} recorded sweeps, "
+                                            f"each queued behind 3 thermalization sweeps"}
+    # the recorded launch alone (the form of the kernel before thermalization and recording
+    # shared a launch), for comparison with the step's single launch
+    result["roofline"]["recorded_launch_alone"] = {
+        "sweeps": SWEEPS_PER_ITER, "ms": pp_s * 1e3,
+        "achieved": OPS_PER_ATTEMPT * pp_rate / 1e12, "frac": OPS_PER_ATTEMPT * pp_rate / 1e12 / peak_tops}
     result["random_site_order"] = {"attempts_per_s": rnd_rate, "ns_per_flip": 1e9 / rnd_rate,
                                    # the same integer-issue roofline as the typewriter kernel
                                    "roofline_frac": OPS_PER_ATTEMPT * rnd_rate / 1e12 / peak_tops,

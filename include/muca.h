@@ -285,6 +285,15 @@ int muca_get_histogram(muca_t h, uint64_t *out, size_t n_bins);
 /* Sets H to zero (asynchronous). */
 int muca_reset_histogram(muca_t h);
 
+/* The sampling of one weight iteration (Sec. 3: N_therm thermalization attempts, then
+ * N_updates recorded ones): zeroes H, then every walker performs n_therm attempts
+ * without recording and n_record recorded attempts.  The results (lattices, energies,
+ * attempt counter, H) equal those of muca_reset_histogram, muca_attempts(h, n_therm, 0)
+ * and muca_attempts(h, n_record, 1).  In typewriter order, when both counts are whole
+ * sweeps starting at a sweep boundary, the two phases run in one kernel launch (the
+ * lattices are read and written once); otherwise as two launches.  Asynchronous. */
+int muca_thermalize_and_record(muca_t h, uint64_t n_therm, uint64_t n_record);
+
 /* The weight iteration of Sec. 2.2 and Sec. 3: repeat { thermalize; zero H; record;
  * stop if H meets the stop rule; else ln W(e) -= ln H(e) where H(e) > 0 (Eq. 4) }.
  * On success the instance holds the weights that produced the flat histogram.

@@ -127,6 +127,7 @@ SIGNATURES = {
     "muca_get_table": (ctypes.c_int, [_H, _P(ctypes.c_uint32), ctypes.c_size_t]),
     "muca_sweep": (ctypes.c_int, [_H, ctypes.c_uint64, ctypes.c_int]),
     "muca_attempts": (ctypes.c_int, [_H, ctypes.c_uint64, ctypes.c_int]),
+    "muca_thermalize_and_record": (ctypes.c_int, [_H, ctypes.c_uint64, ctypes.c_uint64]),
     "muca_get_histogram": (ctypes.c_int, [_H, _P(ctypes.c_uint64), ctypes.c_size_t]),
     "muca_reset_histogram": (ctypes.c_int, [_H]),
     "muca_iterate_until_flat": (ctypes.c_int, [_H, _P(muca_params), _P(muca_stats)]),

@@ -98,25 +98,31 @@ int sync_and_check(muca_t h)
     return check_device_error(h);
 }
 
+static muca::SweepArgs sweep_args(muca_t h, uint64_t n, const uint32_t *skip)
+{
+    muca::SweepArgs a;
+    a.L = h->L;
+    a.layout = h->layout;
+    a.W = h->W;
+    a.seed = h->seed;
+    a.t0 = h->t;
+    a.n = n;
+    a.lattice = h->d_lattice;
+    a.energy = h->d_energy;
+    a.table = h->d_table;
+    a.hist = h->d_hist;
+    a.err = h->d_err;
+    a.skip = skip;
+    a.walker0 = h->walker0;
+    return a;
+}
+
 int run_attempts(muca_t h, uint64_t n, bool record, const uint32_t *skip)
 {
     const uint64_t cap = record ? max_recorded_attempts(h->wpb) : UINT64_MAX;
     while (n > 0) {
         const uint64_t chunk = std::min(n, cap);
-        muca::SweepArgs a;
-        a.L = h->L;
-        a.layout = h->layout;
-        a.W = h->W;
-        a.seed = h->seed;
-        a.t0 = h->t;
-        a.n = chunk;
-        a.lattice = h->d_lattice;
-        a.energy = h->d_energy;
-        a.table = h->d_table;
-        a.hist = h->d_hist;
-        a.err = h->d_err;
-        a.skip = skip;
-        a.walker0 = h->walker0;
+        const muca::SweepArgs a = sweep_args(h, chunk, skip);
         if (h->order == MUCA_ORDER_RANDOM)
             MUCA_CUDA(muca::launch_random_sweep(a, h->wpb, record, h->stream), "random-order sweep launch");
         else
@@ -124,6 +130,20 @@ int run_attempts(muca_t h, uint64_t n, bool record, const uint32_t *skip)
         h->t += chunk;
         n -= chunk;
     }
+    return MUCA_OK;
+}
+
+int run_therm_record(muca_t h, uint64_t n_therm, uint64_t n_record, const uint32_t *skip)
+{
+    if (h->order == MUCA_ORDER_RANDOM || n_therm == 0 || n_record == 0 || n_record > max_recorded_attempts(h->wpb) ||
+        n_therm > UINT64_MAX - n_record) {
+        const int rc = run_attempts(h, n_therm, false, skip);
+        return rc != MUCA_OK ? rc : run_attempts(h, n_record, true, skip);
+    }
+    muca::SweepArgs a = sweep_args(h, n_record, skip);
+    a.n_therm = n_therm;
+    MUCA_CUDA(muca::launch_sweep_fused(a, h->wpb, h->stream), "sweep launch");
+    h->t += n_therm + n_record;
     return MUCA_OK;
 }
 
@@ -610,6 +630,14 @@ int muca_attempts(muca_t h, uint64_t n_attempts, int record)
     if (rc)
         return rc;
     return run_attempts(h, n_attempts, record != 0);
+}
+
+int muca_thermalize_and_record(muca_t h, uint64_t n_therm, uint64_t n_record)
+{
+    int rc = muca_reset_histogram(h);
+    if (rc)
+        return rc;
+    return run_therm_record(h, n_therm, n_record);
 }
 
 int muca_get_histogram(muca_t h, uint64_t *out, size_t n_bins)

@@ -157,13 +157,10 @@ int muca_iterate_until_flat(muca_t h, const muca_params *p_in, muca_stats *stats
         rc = upload_table(h);
         if (rc)
             return rc;
-        rc = run_attempts(h, n_therm, false);
-        if (rc)
-            return rc;
         rc = muca_reset_histogram(h);
         if (rc)
             return rc;
-        rc = run_attempts(h, n_upd, true);
+        rc = run_therm_record(h, n_therm, n_upd);
         if (rc)
             return rc;
         rc = read_reduced_histogram(h, H);
@@ -335,10 +332,8 @@ int muca_iterate_device(muca_t h, const muca_params *p_in, int32_t iterations_pe
     for (;;) {
         const int32_t batch = std::min(iterations_per_sync, p.max_iterations - enqueued);
         for (int32_t i = 0; i < batch; ++i) {
-            if ((rc = run_attempts(h, n_therm, false, done)) != MUCA_OK)
-                return rc;
             MUCA_CUDA(muca::launch_iter_reset_hist(h->d_hist, (int32_t)nb, h->d_iter, h->stream), "histogram reset");
-            if ((rc = run_attempts(h, n_upd, true, done)) != MUCA_OK)
+            if ((rc = run_therm_record(h, n_therm, n_upd, done)) != MUCA_OK)
                 return rc;
             MUCA_CUDA(muca::launch_iter_metric(h->d_iter, N, h->d_hist, p.stop_rule, p.flat_threshold,
                                                p.max_iterations, h->stream),
@@ -398,13 +393,9 @@ int muca_production(muca_t h, uint64_t therm_sweeps, uint64_t n_sweeps, uint64_t
     rc = upload_table(h);
     if (rc)
         return rc;
-    rc = muca_sweep(h, therm_sweeps, 0);
-    if (rc)
-        return rc;
-    rc = muca_reset_histogram(h);
-    if (rc)
-        return rc;
-    rc = muca_sweep(h, n_sweeps, 1);
+    if (therm_sweeps > UINT64_MAX / (uint64_t)N || n_sweeps > UINT64_MAX / (uint64_t)N)
+        return fail(MUCA_EINVAL, "sweep count too large");
+    rc = muca_thermalize_and_record(h, therm_sweeps * (uint64_t)N, n_sweeps * (uint64_t)N);
     if (rc)
         return rc;
     std::vector<uint64_t> H;
@@ -433,15 +424,12 @@ int muca_production_jackknife(muca_t h, uint64_t therm_sweeps, int32_t n_chunks,
     rc = upload_table(h);
     if (rc)
         return rc;
-    rc = muca_sweep(h, therm_sweeps, 0);
-    if (rc)
-        return rc;
+    if (therm_sweeps > UINT64_MAX / (uint64_t)N || sweeps_per_chunk > UINT64_MAX / (uint64_t)N)
+        return fail(MUCA_EINVAL, "sweep count too large");
     std::vector<uint64_t> chunks((size_t)n_chunks * B), total(B, 0), H;
     for (int32_t c = 0; c < n_chunks; ++c) {
-        rc = muca_reset_histogram(h);
-        if (rc)
-            return rc;
-        rc = muca_sweep(h, sweeps_per_chunk, 1);
+        // the thermalization runs with the first chunk
+        rc = muca_thermalize_and_record(h, c == 0 ? therm_sweeps * (uint64_t)N : 0u, sweeps_per_chunk * (uint64_t)N);
         if (rc)
             return rc;
         rc = read_reduced_histogram(h, H);

@@ -161,20 +161,6 @@ __device__ __forceinline__ uint4 philox_walker_c1(uint32_t c0, const PhiloxKeys 
     return make_uint4(x0, x1, x2, x3);
 }
 
-// 32x32 bit transpose across a warp: lane l holds m with bit j = A[l][j]; returns in
-// lane j the word with bit l = A[l][j].  Five butterfly stages of shuffles.
-__device__ __forceinline__ uint32_t warp_transpose32(uint32_t m, int lane)
-{
-    const uint32_t masks[5] = {0x0000FFFFu, 0x00FF00FFu, 0x0F0F0F0Fu, 0x33333333u, 0x55555555u};
-#pragma unroll
-    for (int i = 0; i < 5; ++i) {
-        const int s = 16 >> i;
-        const uint32_t part = __shfl_xor_sync(0xFFFFFFFFu, m, s);
-        m = (lane & s) ? ((m & ~masks[i]) | ((part >> s) & masks[i])) : ((m & masks[i]) | ((part & masks[i]) << s));
-    }
-    return m;
-}
-
 // Sign bits of four int8 spins (-1 = 0xFF, +1 = 0x01) as a nibble.
 __device__ __forceinline__ uint32_t gather_signs(uint32_t v) { return ((v & 0x80808080u) * 0x00204081u) >> 28; }
 
@@ -184,59 +170,88 @@ __device__ __forceinline__ uint32_t spread_signs(uint32_t n)
     return 0x01010101u | (((n * 0x00204081u) & 0x01010101u) * 0xFEu);
 }
 
+// Butterfly stages 8, 4, 2, 1 of a 32x32 bit transpose across a warp: swaps bits 0-3 of
+// the lane index with bits 0-3 of the bit position (bit 4 of each stays in place).
+__device__ __forceinline__ uint32_t warp_swap_low4(uint32_t m, int lane)
+{
+    const uint32_t masks[4] = {0x00FF00FFu, 0x0F0F0F0Fu, 0x33333333u, 0x55555555u};
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+        const int s = 8 >> i;
+        const uint32_t part = __shfl_xor_sync(0xFFFFFFFFu, m, s);
+        m = (lane & s) ? ((m & ~masks[i]) | ((part >> s) & masks[i])) : ((m & masks[i]) | ((part & masks[i]) << s));
+    }
+    return m;
+}
+
+// Sign bits of 16 int8 spins as a 16-bit mask (bit i = byte i).
+__device__ __forceinline__ uint32_t gather16(uint4 u)
+{
+    return gather_signs(u.x) | (gather_signs(u.y) << 4) | (gather_signs(u.z) << 8) | (gather_signs(u.w) << 12);
+}
+
 // Bit rows of the warp's 32 walkers from the int8 [site][walker] layout, R rows at a
 // time so that their loads are in flight together; lane j receives walker w0 + j.
+// Lanes 2p and 2p + 1 read the two halves of one site's 32 walker bytes (sites 32h + p and
+// 32h + 16 + p of row half h), so each load instruction covers 16 whole 32-byte sectors.
+// Lane 2p + q then holds bit 16r + s = spin of walker 16q + s at site 32h + 16r + p; a
+// lane shuffle to lane 16q + p and four butterfly stages (lane bits 0-3 against bit
+// positions 0-3) leave in lane 16q + s the spins of walker 16q + s, bit x at site 32h + x.
 // All 32 walkers must exist and W % 16 == 0.
 template <int L, int R, typename RowT>
 __device__ __forceinline__ void warp_load_rows_int8(const int8_t *g, int64_t W, int64_t w0, int y0, int lane,
                                                     RowT (&out)[R])
 {
     constexpr int HALVES = (L + 31) / 32;
+    const int p = lane >> 1, q = lane & 1;
     uint4 a[R][HALVES], b[R][HALVES];
 #pragma unroll
     for (int r = 0; r < R; ++r)
 #pragma unroll
         for (int half = 0; half < HALVES; ++half) {
-            const int x = half * 32 + lane;
-            if (x < L) {
-                const uint4 *p = reinterpret_cast<const uint4 *>(g + (size_t)((y0 + r) * L + x) * (size_t)W + (size_t)w0);
-                a[r][half] = p[0];
-                b[r][half] = p[1];
-            } else {
-                a[r][half] = make_uint4(0, 0, 0, 0);
-                b[r][half] = make_uint4(0, 0, 0, 0);
-            }
+            const int xa = half * 32 + p, xb = xa + 16;
+            const int8_t *row = g + (size_t)((y0 + r) * L) * (size_t)W + (size_t)w0 + 16 * q;
+            a[r][half] = xa < L ? *reinterpret_cast<const uint4 *>(row + (size_t)xa * (size_t)W) : make_uint4(0, 0, 0, 0);
+            b[r][half] = xb < L ? *reinterpret_cast<const uint4 *>(row + (size_t)xb * (size_t)W) : make_uint4(0, 0, 0, 0);
         }
+    const int src = 2 * (lane & 15) + (lane >> 4);
 #pragma unroll
     for (int r = 0; r < R; ++r) {
         RowT row = 0;
 #pragma unroll
         for (int half = 0; half < HALVES; ++half) {
-            const uint4 u = a[r][half], v = b[r][half];
-            uint32_t m = gather_signs(u.x) | (gather_signs(u.y) << 4) | (gather_signs(u.z) << 8) |
-                         (gather_signs(u.w) << 12) | (gather_signs(v.x) << 16) | (gather_signs(v.y) << 20) |
-                         (gather_signs(v.z) << 24) | (gather_signs(v.w) << 28);
-            m = warp_transpose32(m, lane);
+            uint32_t m = gather16(a[r][half]) | (gather16(b[r][half]) << 16);
+            m = __shfl_sync(0xFFFFFFFFu, m, src);
+            m = warp_swap_low4(m, lane);
             row |= (RowT)m << (32 * half);
         }
         out[r] = row;
     }
 }
 
+// 16 spins of a 16-bit mask (bit i = byte i, set = -1) as int8.
+__device__ __forceinline__ uint4 scatter16(uint32_t h)
+{
+    return make_uint4(spread_signs(h & 15u), spread_signs((h >> 4) & 15u), spread_signs((h >> 8) & 15u),
+                      spread_signs((h >> 12) & 15u));
+}
+
+// The inverse of warp_load_rows_int8 for one row: lane j holds walker w0 + j's bits.
 template <int L, typename RowT>
 __device__ __forceinline__ void warp_store_row_int8(int8_t *g, int64_t W, int64_t w0, int y, int lane, RowT r)
 {
+    const int p = lane >> 1, q = lane & 1;
+    const int src = 16 * q + p;
 #pragma unroll
     for (int half = 0; half < (L + 31) / 32; ++half) {
-        const uint32_t m = warp_transpose32((uint32_t)(r >> (32 * half)), lane);
-        const int x = half * 32 + lane;
-        if (x < L) {
-            uint4 *p = reinterpret_cast<uint4 *>(g + (size_t)(y * L + x) * (size_t)W + (size_t)w0);
-            p[0] = make_uint4(spread_signs(m & 15u), spread_signs((m >> 4) & 15u), spread_signs((m >> 8) & 15u),
-                              spread_signs((m >> 12) & 15u));
-            p[1] = make_uint4(spread_signs((m >> 16) & 15u), spread_signs((m >> 20) & 15u),
-                              spread_signs((m >> 24) & 15u), spread_signs(m >> 28));
-        }
+        uint32_t m = warp_swap_low4((uint32_t)(r >> (32 * half)), lane);
+        m = __shfl_sync(0xFFFFFFFFu, m, src);
+        const int xa = half * 32 + p, xb = xa + 16;
+        int8_t *row = g + (size_t)(y * L) * (size_t)W + (size_t)w0 + 16 * q;
+        if (xa < L)
+            *reinterpret_cast<uint4 *>(row + (size_t)xa * (size_t)W) = scatter16(m & 0xFFFFu);
+        if (xb < L)
+            *reinterpret_cast<uint4 *>(row + (size_t)xb * (size_t)W) = scatter16(m >> 16);
     }
 }
 
@@ -766,16 +781,22 @@ __device__ __forceinline__ void sweep_block(const SweepArgs &a, int64_t wbase, i
     bool active = in_item && w < a.W;
     const bool warp_full = in_item && (w0 + 32 <= a.W) && (a.W % 16 == 0);
 
-    if (GUARD) {
+    // the thresholds as asynchronous 4-byte copies (all in flight together and behind the
+    // lattice load; waited for before the barrier), the other words of the table zeroed
+    {
+        const uint32_t sbase = (uint32_t)__cvta_generic_to_shared(sTab);
+        for (int i = tid; i < NB * 5; i += nthr) {
+            const int e = i / 5, k = i - e * 5;
+            asm volatile("cp.async.ca.shared.global [%0], [%1], 4;" ::"r"(sbase + 4u * (uint32_t)((e + G) * STRIDE + k)),
+                         "l"(a.table + i)
+                         : "memory");
+        }
+        asm volatile("cp.async.commit_group;" ::: "memory");
         for (int i = tid; i < NR * STRIDE; i += nthr) {
             const int r = i / STRIDE, k = i - r * STRIDE;
             const int e = r - G;
-            sTab[i] = (k < 5 && e >= 0 && e <= N) ? a.table[e * 5 + k] : 0u;
-        }
-    } else {
-        for (int i = tid; i < NB * STRIDE; i += nthr) {
-            const int e = i / STRIDE, k = i - e * STRIDE;
-            sTab[i] = k < 5 ? a.table[e * 5 + k] : 0u;
+            if (k >= 5 || e < 0 || e > N)
+                sTab[i] = 0u;
         }
     }
 
@@ -808,13 +829,42 @@ __device__ __forceinline__ void sweep_block(const SweepArgs &a, int64_t wbase, i
             active = false;
         }
     }
+    asm volatile("cp.async.wait_all;" ::: "memory");
     __syncthreads();
 
-    if (active) {
-        const PhiloxKeys pk = make_keys(a.seed, a.walker0 + (uint32_t)w, (uint32_t)(a.t0 >> 34));
-        const uint32_t tbase = (uint32_t)__cvta_generic_to_shared(sTab) + G * STRIDE * 4u;
-        uint32_t U[NW], C[NW], D[NW];
-        uint32_t E = tbase + (uint32_t)e * (4u * STRIDE);
+    const PhiloxKeys pk = make_keys(a.seed, a.walker0 + (uint32_t)w, (uint32_t)(a.t0 >> 34));
+    const uint32_t tbase = (uint32_t)__cvta_generic_to_shared(sTab) + G * STRIDE * 4u;
+    uint32_t U[NW], C[NW], D[NW];
+    uint32_t E = tbase + (uint32_t)e * (4u * STRIDE);
+    if (C1_ONLY && !PARTIAL) {
+        // whole sweeps from a sweep boundary, counter word 1 (t >> 34) fixed for the launch
+        // (launch_sweep splits launches at its steps).  A recording launch may carry a
+        // thermalization phase in front (n_therm attempts): the same attempt stream, its
+        // counts added to the histogram words and cleared before the recorded phase, so
+        // that the launch equals a thermalization launch followed by a recording one.
+        // Both phases run the one inlined copy of the sweep loop.
+        if (active) {
+            rows.load(L - 1, U);
+            rows.load(0, C);
+            rows.load(1, D);
+        }
+        const bool fused = RECORD && a.n_therm > 0;   // uniform over the launch
+        uint64_t blk = a.t0 >> 2;
+        uint64_t ns = (fused ? a.n_therm : a.n) / (uint64_t)N;
+#pragma unroll 1
+        for (int phase = fused ? 0 : 1; phase < 2; ++phase) {
+            if (active)
+                whole_sweeps_c1<L, RECORD, STRIDE>(rows, U, C, D, E, blk, ns, pk);
+            if (phase == 0) {
+                __syncthreads();
+                for (int i = tid; i < NB; i += nthr)
+                    sTab[(i + G) * STRIDE + kHistSlot] = 0u;
+                __syncthreads();
+                blk += ns * (uint64_t)(N / 4);
+                ns = a.n / (uint64_t)N;
+            }
+        }
+    } else if (active) {
         if (!PARTIAL) {
             // whole sweeps from a sweep boundary; counter word 1 (t >> 34) is the same for
             // every attempt of the launch except in the rare launch that crosses a step
@@ -889,6 +939,8 @@ __device__ __forceinline__ void sweep_block(const SweepArgs &a, int64_t wbase, i
                 rows.store(y, C);
             }
         }
+    }
+    if (active) {
         e = (int32_t)((E - tbase) / (4u * STRIDE));
         if (E < tbase || e > N || (E - tbase) % (4u * STRIDE) != 0u)   // corrupted energy address
             atomicOr(a.err, kErrEnergyRange);

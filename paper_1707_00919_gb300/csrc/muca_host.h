@@ -100,6 +100,9 @@ int upload_table(muca_t h);
 int check_device_error(muca_t h);
 int sync_and_check(muca_t h);
 int run_attempts(muca_t h, uint64_t n, bool record, const uint32_t *skip = nullptr);
+// n_therm attempts without recording, then n_record recorded ones (the histogram is not
+// zeroed here); one kernel launch where the whole-sweep kernel allows it.
+int run_therm_record(muca_t h, uint64_t n_therm, uint64_t n_record, const uint32_t *skip = nullptr);
 int read_histogram(muca_t h, std::vector<uint64_t> &H);
 // The instance's histogram, or its sum over the instances of the simulation when a reducer is set.
 int read_reduced_histogram(muca_t h, std::vector<uint64_t> &H);

@@ -40,6 +40,10 @@ struct SweepArgs {
     uint32_t *err;              // device error word
     const uint32_t *skip = nullptr;   // when set and nonzero at launch: the launch does nothing
     uint32_t walker0 = 0;             // global index of walker 0 (the Philox walker word is walker0 + w)
+    // Thermalization attempts run before the launch's n recorded ones, from t0 (the
+    // recorded attempts then start at t0 + n_therm).  Only a recording whole-sweep launch
+    // (launch_sweep_fused) sets it; every other launch leaves it 0.
+    uint64_t n_therm = 0;
 };
 
 // Device state of an iteration whose recursion runs on the device (muca_iterate_device).
@@ -87,6 +91,10 @@ size_t sweep_smem_limit();
 // L (L in {8, 16, 24, 32, 48, 64}; whole sweeps or, with its partial-row path, any
 // range), the generic kernel for other L.  Grid = ceil(W / walkers_per_block).
 cudaError_t launch_sweep(const SweepArgs &a, int walkers_per_block, bool record, cudaStream_t s);
+// a.n_therm thermalization attempts from a.t0, then a.n recorded ones: one launch of the
+// whole-sweep kernel where both are whole sweeps from a sweep boundary within one step of
+// counter word 1, else a thermalization launch and a recording launch.
+cudaError_t launch_sweep_fused(const SweepArgs &a, int walkers_per_block, cudaStream_t s);
 
 // Runs attempts [t0, t0 + n) of every walker in random shared site order (muca_random.cu;
 // any L, any attempt range; the given block size, or a smaller one that fits shared

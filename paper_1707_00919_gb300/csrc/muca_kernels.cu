@@ -373,6 +373,24 @@ cudaError_t launch_sweep(const SweepArgs &a, int wpb, bool record, cudaStream_t 
     return launch_full(a, wpb, record, s);
 }
 
+cudaError_t launch_sweep_fused(const SweepArgs &a, int wpb, cudaStream_t s)
+{
+    const uint64_t N = (uint64_t)a.L * (uint64_t)a.L;
+    const uint64_t total = a.n_therm + a.n;
+    // one launch: whole sweeps from a sweep boundary in the whole-sweep kernel, counter
+    // word 1 (t >> 34) the same for both phases
+    if (a.W > 0 && a.n_therm > 0 && a.n > 0 && has_full_kernel(a.L) && g_use_full_kernel && a.t0 % N == 0 &&
+        a.n_therm % N == 0 && a.n % N == 0 && total > a.n && (a.t0 >> 34) == ((a.t0 + total - 1) >> 34))
+        return launch_full(a, wpb, true, s);
+    SweepArgs therm = a, rec = a;
+    therm.n = a.n_therm;
+    therm.n_therm = 0;
+    rec.t0 = a.t0 + a.n_therm;
+    rec.n_therm = 0;
+    const cudaError_t err = launch_sweep(therm, wpb, false, s);
+    return err != cudaSuccess ? err : launch_sweep(rec, wpb, true, s);
+}
+
 void set_full_kernel_enabled(bool on) { g_use_full_kernel = on; }
 
 cudaError_t launch_init(int32_t L, int32_t layout, int64_t W, uint64_t seed, uint32_t walker0, void *lattice,

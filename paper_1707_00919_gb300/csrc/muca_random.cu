@@ -68,25 +68,26 @@ __device__ __forceinline__ void hist_count(uint32_t E)
 }
 
 // Bit rows of a warp's 32 walkers from the int8 [site][walker] layout, four rows at a
-// time (their 16-byte loads in flight together): lane j receives walker w0 + j.  All 32
+// time (their 16-byte loads in flight together): lane j receives walker w0 + j.  As in
+// warp_load_rows_int8, lanes 2p and 2p + 1 read the two halves of one site's 32 walker
+// bytes, and a lane shuffle plus four butterfly stages complete the transpose.  All 32
 // walkers must exist and W % 16 == 0; L is a multiple of 4 up to 64.
 template <typename RowT>
 __device__ __forceinline__ void warp_load_rows(const int8_t *g, int64_t W, int64_t w0, int L, int y0, int lane,
                                                RowT (&out)[4])
 {
+    const int p = lane >> 1, q = lane & 1;
     uint4 va[4][2], vb[4][2];
 #pragma unroll
     for (int r = 0; r < 4; ++r)
 #pragma unroll
         for (int half = 0; half < 2; ++half) {
-            const int x = half * 32 + lane;
-            va[r][half] = vb[r][half] = make_uint4(0u, 0u, 0u, 0u);
-            if (x < L) {
-                const uint4 *p = reinterpret_cast<const uint4 *>(g + (size_t)((y0 + r) * L + x) * (size_t)W + (size_t)w0);
-                va[r][half] = p[0];
-                vb[r][half] = p[1];
-            }
+            const int xa = half * 32 + p, xb = xa + 16;
+            const int8_t *row = g + (size_t)((y0 + r) * L) * (size_t)W + (size_t)w0 + 16 * q;
+            va[r][half] = xa < L ? *reinterpret_cast<const uint4 *>(row + (size_t)xa * (size_t)W) : make_uint4(0u, 0u, 0u, 0u);
+            vb[r][half] = xb < L ? *reinterpret_cast<const uint4 *>(row + (size_t)xb * (size_t)W) : make_uint4(0u, 0u, 0u, 0u);
         }
+    const int src = 2 * (lane & 15) + (lane >> 4);
 #pragma unroll
     for (int r = 0; r < 4; ++r) {
         RowT row = 0;
@@ -94,11 +95,9 @@ __device__ __forceinline__ void warp_load_rows(const int8_t *g, int64_t W, int64
         for (int half = 0; half < 2; ++half) {
             if (half * 32 >= L)   // uniform over the warp
                 break;
-            const uint4 u = va[r][half], v = vb[r][half];
-            uint32_t m = gather_signs(u.x) | (gather_signs(u.y) << 4) | (gather_signs(u.z) << 8) |
-                         (gather_signs(u.w) << 12) | (gather_signs(v.x) << 16) | (gather_signs(v.y) << 20) |
-                         (gather_signs(v.z) << 24) | (gather_signs(v.w) << 28);
-            m = warp_transpose32(m, lane);
+            uint32_t m = gather16(va[r][half]) | (gather16(vb[r][half]) << 16);
+            m = __shfl_sync(0xFFFFFFFFu, m, src);
+            m = warp_swap_low4(m, lane);
             row |= (RowT)m << (32 * half);
         }
         out[r] = row;
@@ -108,19 +107,20 @@ __device__ __forceinline__ void warp_load_rows(const int8_t *g, int64_t W, int64
 template <typename RowT>
 __device__ __forceinline__ void warp_store_row(int8_t *g, int64_t W, int64_t w0, int L, int y, int lane, RowT r)
 {
+    const int p = lane >> 1, q = lane & 1;
+    const int src = 16 * q + p;
 #pragma unroll
     for (int half = 0; half < 2; ++half) {
         if (half * 32 >= L)   // uniform over the warp
             break;
-        const uint32_t m = warp_transpose32((uint32_t)(r >> (32 * half)), lane);
-        const int x = half * 32 + lane;
-        if (x < L) {
-            uint4 *p = reinterpret_cast<uint4 *>(g + (size_t)(y * L + x) * (size_t)W + (size_t)w0);
-            p[0] = make_uint4(spread_signs(m & 15u), spread_signs((m >> 4) & 15u), spread_signs((m >> 8) & 15u),
-                              spread_signs((m >> 12) & 15u));
-            p[1] = make_uint4(spread_signs((m >> 16) & 15u), spread_signs((m >> 20) & 15u),
-                              spread_signs((m >> 24) & 15u), spread_signs(m >> 28));
-        }
+        uint32_t m = warp_swap_low4((uint32_t)(r >> (32 * half)), lane);
+        m = __shfl_sync(0xFFFFFFFFu, m, src);
+        const int xa = half * 32 + p, xb = xa + 16;
+        int8_t *row = g + (size_t)(y * L) * (size_t)W + (size_t)w0 + 16 * q;
+        if (xa < L)
+            *reinterpret_cast<uint4 *>(row + (size_t)xa * (size_t)W) = scatter16(m & 0xFFFFu);
+        if (xb < L)
+            *reinterpret_cast<uint4 *>(row + (size_t)xb * (size_t)W) = scatter16(m >> 16);
     }
 }
 

@@ -212,6 +212,10 @@ def muca_attempts(h, n_attempts: int, record: bool) -> None:
     _check(C.load().muca_attempts(h, n_attempts, 1 if record else 0))
 
 
+def muca_thermalize_and_record(h, n_therm: int, n_record: int) -> None:
+    _check(C.load().muca_thermalize_and_record(h, n_therm, n_record))
+
+
 def muca_get_histogram(h, n_bins: int) -> np.ndarray:
     a = np.zeros(n_bins, dtype=np.uint64)
     _check(C.load().muca_get_histogram(h, _p(a, ctypes.c_uint64), n_bins))
@@ -472,6 +476,10 @@ class Muca:
 
     def attempts(self, n_attempts: int, record: bool = True) -> None:
         muca_attempts(self._h, n_attempts, record)
+
+    def thermalize_and_record(self, n_therm: int, n_record: int) -> None:
+        """Zeroed H, n_therm attempts per walker unrecorded, then n_record recorded."""
+        muca_thermalize_and_record(self._h, n_therm, n_record)
 
     def get_histogram(self) -> np.ndarray:
         return muca_get_histogram(self._h, self.n_bins)
