@@ -9,7 +9,8 @@ Reported:
   value        spin-flip attempts per second over K weight-iteration steps (one step =
                table build + upload, thermalization, zeroed histogram, recorded sweeps,
                histogram read, flatness test and Eq. (4) recursion), device-timed with
-               CUDA events, L2 flushed between steps;
+               CUDA events, L2 flushed in each timed step before its sweep launch (the
+               flush's window is not counted);
   time_to_flat wall time of muca_iterate_until_flat from ln W = 0 until min/mean >= 0.8;
   e2e          the same steps through the C ABI with host weights in and the host
                histogram out (copies inside the timed region), host wall clock;
@@ -47,10 +48,10 @@ MAX_ITERATIONS = 2 * 10**4 * L_SIDE * L_SIDE // (WALKERS * SWEEPS_PER_ITER)   # 
 # load, compare, conditional flip, energy update, run-length histogram record, about
 # 15.5).  Fixed by the method, not measured from the code.
 OPS_PER_ATTEMPT = 35.0
-# Warp instructions the recorded whole-sweep kernel issues per attempt and warp (ncu
+# Warp instructions the step's whole-sweep launch issues per attempt and warp (ncu
 # count, profiles/sweep_full_kernel_L32_W16384_int8.md): converts an instruction issue
 # rate into this roofline's algorithmic operations.
-INSTR_PER_ATTEMPT = 33.6
+INSTR_PER_ATTEMPT = 33.05
 WORKLOAD = (f"muca2d_ising_L{L_SIDE}_W{WALKERS}_int8_therm{THERM_SWEEPS}_rec{SWEEPS_PER_ITER}")
 
 
@@ -58,7 +59,7 @@ def config_dict():
     return {"workload": WORKLOAD, "L": L_SIDE, "walkers": WALKERS, "layout": "int8 [site][walker]",
             "therm_sweeps": THERM_SWEEPS, "sweeps_per_iter": SWEEPS_PER_ITER, "energy_bins": L_SIDE**2 + 1,
             "stop_rule": "min/mean >= 0.8", "max_iterations": MAX_ITERATIONS,
-            "l2": "flushed between timed steps (256 MiB write)", "parallelism": "independent instance per GPU",
+            "l2": "flushed in every timed step before its sweep launch (256 MiB write, its window not counted)", "parallelism": "independent instance per GPU",
             "arithmetic": "u32 thresholds, random words and counts; int8 spins; u64 histogram; f64 weights"}
 
 
@@ -412,22 +413,28 @@ def run_native(args):
         """One weight iteration through the C ABI (table build and upload; zeroed
         histogram, thermalization and recorded sweeps in one muca_thermalize_and_record
         call, one kernel launch; histogram read; the min/mean flatness test and the
-        Eq. (4) recursion, muca_flatness and muca_update_weights); ev = four CUDA events
-        on the instance's stream: step start, before the sampling call, after it, and
-        after the host recursion (so a step's time includes the host work)."""
+        Eq. (4) recursion, muca_flatness and muca_update_weights).  ev = five CUDA events
+        on the instance's stream: step start, the L2 flush's start and end, after the
+        sampling call, after the host recursion.  In a timed step the L2 flush (a 256 MiB
+        write) runs between the table upload and the sampling call: the GPU is busy with
+        it while the host enqueues the launch, so that the sampling window holds GPU work
+        only; the flush's own window is left out of the step's time."""
         if ev:
             ev[0].record(stream)
         m.set_weights(lnW)
         if ev:
             ev[1].record(stream)
+            with torch.cuda.stream(stream):
+                flush.zero_()
+            ev[2].record(stream)
         m.thermalize_and_record(THERM_SWEEPS * N, SWEEPS_PER_ITER * N)
         if ev:
-            ev[2].record(stream)
+            ev[3].record(stream)
         H = m.get_histogram()
         flat[0] = M.muca_flatness(L_SIDE, H)["min_over_mean"] >= 0.8
         M.muca_update_weights(L_SIDE, lnW, H)
         if ev:
-            ev[3].record(stream)
+            ev[4].record(stream)
         return H
 
     # NVTX range around the warm-up and timed steps, so that a profiler can be limited to
@@ -439,21 +446,19 @@ def run_native(args):
             flush.zero_()
     stream.synchronize()
 
-    evs = [[torch.cuda.Event(enable_timing=True) for _ in range(4)] for _ in range(args.steps)]
+    evs = [[torch.cuda.Event(enable_timing=True) for _ in range(5)] for _ in range(args.steps)]
     barrier(dist)
     torch.cuda.synchronize()
     t_timed0 = time.perf_counter()
     for k in range(args.steps):
         step(evs[k])
-        with torch.cuda.stream(stream):
-            flush.zero_()
     stream.synchronize()
     torch.cuda.synchronize()
     t_timed1 = time.perf_counter()
     torch.cuda.nvtx.range_pop()
-    step_ms = [evs[k][0].elapsed_time(evs[k][3]) for k in range(args.steps)]
+    step_ms = [evs[k][0].elapsed_time(evs[k][4]) - evs[k][1].elapsed_time(evs[k][2]) for k in range(args.steps)]
     table_ms = [evs[k][0].elapsed_time(evs[k][1]) for k in range(args.steps)]
-    sample_ms = [evs[k][1].elapsed_time(evs[k][2]) for k in range(args.steps)]
+    sample_ms = [evs[k][2].elapsed_time(evs[k][3]) for k in range(args.steps)]
     total_s = sum(step_ms) / 1e3
     total_s = max_over_ranks(dist, total_s)
     barrier(dist)
