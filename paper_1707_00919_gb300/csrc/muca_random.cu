@@ -287,7 +287,10 @@ __global__ void __launch_bounds__(256) random_sweep_kernel(const SweepArgs a)
             uint32_t kc1 = count(b1, row(c1.x & ~kCleanBit), row(c1.y), row(c1.z));
             uint32_t kc2 = count(b2, row(c2.x & ~kCleanBit), row(c2.y), row(c2.z));
             uint32_t kc3 = count(b3, row(c3.x & ~kCleanBit), row(c3.y), row(c3.z));
+            uint4 qn = words(t);
             for (; m - j >= 4; j += 4, t += 4) {
+                const uint4 qg = qn;
+                qn = words(t + 4);   // the next group's words, ahead of its decisions
                 // the next group's sites and rows, read before this group's flips
                 const uint4 n0 = sSite[j + 4], n1 = sSite[j + 5], n2 = sSite[j + 6], n3 = sSite[j + 7];
                 const uint4 p0 = sMask[j + 4], p1 = sMask[j + 5], p2 = sMask[j + 6], p3 = sMask[j + 7];
@@ -296,7 +299,8 @@ __global__ void __launch_bounds__(256) random_sweep_kernel(const SweepArgs a)
                 const RowT u2 = row(n2.x & ~kCleanBit), m2 = row(n2.y), d2r = row(n2.z);
                 const RowT u3 = row(n3.x & ~kCleanBit), m3 = row(n3.y), d3r = row(n3.z);
                 // the next group's counts; computed inside each branch below, so that the
-                // scheduler can place them (and the Philox rounds) between the decisions
+                // scheduler can place them (and the next group's Philox rounds, started
+                // above) between the decisions
                 auto next_counts = [&]() {
                     kc0 = count(p0, u0, m0, d0r);
                     kc1 = count(p1, u1, m1, d1r);
@@ -304,7 +308,7 @@ __global__ void __launch_bounds__(256) random_sweep_kernel(const SweepArgs a)
                     kc3 = count(p3, u3, m3, d3r);
                 };
                 if (c0.x & kCleanBit) {
-                    const uint4 q = words(t);
+                    const uint4 q = qg;
                     // Each decision takes one of two thresholds loaded one attempt
                     // ahead (the previous attempt rejected / flipped); the counts are
                     // known for the whole group.
@@ -336,7 +340,7 @@ __global__ void __launch_bounds__(256) random_sweep_kernel(const SweepArgs a)
                         hist_count(E);
                     next_counts();
                 } else {
-                    const uint4 q = words(t);
+                    const uint4 q = qg;
                     single(j, q.x);
                     single(j + 1, q.y);
                     single(j + 2, q.z);
