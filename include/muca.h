@@ -407,9 +407,10 @@ int muca_batch_sweep(muca_batch_t b, uint64_t n_sweeps, int record);
 /* The weight iteration of muca_iterate_until_flat for every member at once (either
  * schedule; with MUCA_SCHEDULE_PAPER each member follows Eq. (7) from its own visited
  * ranges, and launches may start and end inside sweeps).  Each iteration is one replay of
- * a CUDA graph (table uploads, thermalization launch, zeroed histograms, recording
- * launch, histogram reads), or, when a member records more than 0xFFFFFFFF / 256
- * attempts per walker, the same steps issued directly with several recording launches;
+ * a CUDA graph (table uploads, zeroed histograms, one launch in which every member's
+ * walkers thermalize and then record, histogram reads), or, when a member records more
+ * than 0xFFFFFFFF / 256 attempts per walker, the same steps issued directly with a
+ * thermalization launch and several recording launches;
  * a member leaves the work list when its histogram is flat or it reached max_iterations.
  * stats[i] (may be NULL) receives member i's result, seconds being the wall time until
  * its last iteration finished.  Returns MUCA_OK if every member became flat, else

@@ -102,8 +102,9 @@ int check_members(muca_batch_t b)
 }
 
 // Captures one weight iteration of the current members: table uploads, the launch
-// descriptors, thermalization launch, zeroed histograms, recording launch, histogram
-// and error-word reads.  The host refills the pinned buffers before every replay.
+// descriptors, zeroed histograms, one launch that runs every member's thermalization and
+// then its recorded attempts (the recording descriptors carry n_therm), histogram and
+// error-word reads.  The host refills the pinned buffers before every replay.
 int build_graph(muca_batch_t b)
 {
     if (b->exec) {
@@ -125,8 +126,6 @@ int build_graph(muca_batch_t b)
                               b->stream);
     if (err == cudaSuccess)
         err = cudaMemsetAsync(b->d_counter, 0, 2 * sizeof(uint32_t), b->stream);
-    if (err == cudaSuccess)
-        err = muca::launch_batch(b->d_args, b->d_items, b->n_items, b->d_counter, b->grid, b->smem, false, b->stream);
     for (int32_t j : b->members) {
         const muca_t h = b->inst[(size_t)j];
         if (err == cudaSuccess)
@@ -239,7 +238,12 @@ int batch_run_iteration(muca_batch_t b, const std::vector<int32_t> &active, cons
         muca_t h = b->inst[(size_t)active[j]];
         build_table(h->L, h->lnW, h->h_table);
         b->h_args[j] = make_args(h, h->t, therm[j]);
-        b->h_args[nm + j] = make_args(h, h->t + therm[j], std::min(rec[j], cap));
+        if (chunked) {   // a thermalization launch, then recording launches of at most cap attempts
+            b->h_args[nm + j] = make_args(h, h->t + therm[j], std::min(rec[j], cap));
+        } else {         // one launch: the thermalization in front of the recorded attempts
+            b->h_args[nm + j] = make_args(h, h->t, rec[j]);
+            b->h_args[nm + j].n_therm = therm[j];
+        }
     }
     if (!chunked) {
         MUCA_CUDA(cudaGraphLaunch(b->exec, b->stream), "batch iteration launch");

@@ -864,79 +864,97 @@ __device__ __forceinline__ void sweep_block(const SweepArgs &a, int64_t wbase, i
                 ns = a.n / (uint64_t)N;
             }
         }
-    } else if (active) {
-        if (!PARTIAL) {
-            // whole sweeps from a sweep boundary; counter word 1 (t >> 34) is the same for
-            // every attempt of the launch except in the rare launch that crosses a step
-            // of it, which takes the general generator throughout (kernels whose launches
-            // never cross one compile only the first)
-            rows.load(L - 1, U);
-            rows.load(0, C);
-            rows.load(1, D);
-            if (C1_ONLY || (a.t0 >> 34) == ((a.t0 + a.n - 1) >> 34))
-                whole_sweeps_c1<L, RECORD, STRIDE>(rows, U, C, D, E, a.t0 >> 2, a.n / (uint64_t)N, pk);
-            else
-                whole_sweeps<L, RECORD, STRIDE>(rows, U, C, D, E, a.t0 >> 2, a.n / (uint64_t)N, pk);
-        } else {
-            // any attempt range: a first row cut by the launch's start and a last row cut
-            // by its end run masked, the whole rows between them as one attempt stream
-            uint64_t t = a.t0;
-            const uint64_t tend = a.t0 + a.n;
-            int y = (int)((t % (uint64_t)N) / L);
-            const int x0 = (int)((t % (uint64_t)N) % L);
-            uint64_t blk = (t - (uint64_t)x0) >> 2;   // Philox block of column 0 of row y
-            rows.load((y + L - 1) % L, U);
-            rows.load(y, C);
-            rows.load((y + 1) % L, D);
-            bool ended = false;
-            if (x0 != 0 || tend - t < (uint64_t)L) {
-                const uint64_t left = tend - t;
-                const int xe = left < (uint64_t)(L - x0) ? x0 + (int)left : L;
-                const PhiloxSource src{blk, &pk};
-                process_row<L, RECORD, true, PhiloxSource, STRIDE>(U, C, D, E, src, x0, xe);
-                rows.store(y, C);
-                t += (uint64_t)(xe - x0);
-                ended = xe < L;   // the launch ends inside this row
-                if (!ended) {
-                    const int y2 = (y + 2 < L) ? y + 2 : y + 2 - L;
-#pragma unroll
-                    for (int i = 0; i < NW; ++i) {
-                        U[i] = C[i];
-                        C[i] = D[i];
-                    }
-                    rows.load(y2, D);
-                    y = (y + 1 == L) ? 0 : y + 1;
-                    blk += (uint64_t)(L / 4);
-                }
-            }
-            const uint64_t nwhole = ended ? 0u : (tend - t) / (uint64_t)L;
-            if (nwhole > 0) {
-                if (C1_ONLY || (a.t0 >> 34) == ((a.t0 + a.n - 1) >> 34)) {
-                    stream_rows_c1<L, RECORD, STRIDE>(rows, U, C, D, E, blk, y, nwhole, pk);
-                } else {
+    } else {
+        // every other form (the general generator, any attempt range, the batched
+        // kernels): a recording launch may carry a thermalization phase in front here too
+        // (a.n_therm attempts from a.t0, any range), its counts cleared between the phases
+        const bool fused = RECORD && a.n_therm > 0;   // uniform over the launch
 #pragma unroll 1
-                    for (uint64_t r = 0; r < nwhole; ++r) {
-                        const PhiloxSource src{blk + r * (uint64_t)(L / 4), &pk};
-                        const int yr = (int)(((uint64_t)y + r) % (uint64_t)L);
-                        process_row<L, RECORD, false, PhiloxSource, STRIDE>(U, C, D, E, src);
-                        rows.store(yr, C);
-                        const int y2 = (yr + 2 < L) ? yr + 2 : yr + 2 - L;
-#pragma unroll
-                        for (int i = 0; i < NW; ++i) {
-                            U[i] = C[i];
-                            C[i] = D[i];
+        for (int phase = fused ? 0 : 1; phase < 2; ++phase) {
+            const uint64_t t0p = phase == 0 ? a.t0 : a.t0 + (fused ? a.n_therm : 0u);
+            const uint64_t np = phase == 0 ? a.n_therm : a.n;
+            if (active && np > 0) {
+                const PhiloxKeys pkp = make_keys(a.seed, a.walker0 + (uint32_t)w, (uint32_t)(t0p >> 34));
+                if (!PARTIAL) {
+                    // whole sweeps from a sweep boundary; counter word 1 (t >> 34) is the same
+                    // for every attempt of the range except in the rare range that crosses a
+                    // step of it, which takes the general generator throughout (kernels whose
+                    // launches never cross one compile only the first)
+                    rows.load(L - 1, U);
+                    rows.load(0, C);
+                    rows.load(1, D);
+                    if (C1_ONLY || (t0p >> 34) == ((t0p + np - 1) >> 34))
+                        whole_sweeps_c1<L, RECORD, STRIDE>(rows, U, C, D, E, t0p >> 2, np / (uint64_t)N, pkp);
+                    else
+                        whole_sweeps<L, RECORD, STRIDE>(rows, U, C, D, E, t0p >> 2, np / (uint64_t)N, pkp);
+                } else {
+                    // any attempt range: a first row cut by the launch's start and a last row cut
+                    // by its end run masked, the whole rows between them as one attempt stream
+                    uint64_t t = t0p;
+                    const uint64_t tend = t0p + np;
+                    int y = (int)((t % (uint64_t)N) / L);
+                    const int x0 = (int)((t % (uint64_t)N) % L);
+                    uint64_t blk = (t - (uint64_t)x0) >> 2;   // Philox block of column 0 of row y
+                    rows.load((y + L - 1) % L, U);
+                    rows.load(y, C);
+                    rows.load((y + 1) % L, D);
+                    bool ended = false;
+                    if (x0 != 0 || tend - t < (uint64_t)L) {
+                        const uint64_t left = tend - t;
+                        const int xe = left < (uint64_t)(L - x0) ? x0 + (int)left : L;
+                        const PhiloxSource src{blk, &pkp};
+                        process_row<L, RECORD, true, PhiloxSource, STRIDE>(U, C, D, E, src, x0, xe);
+                        rows.store(y, C);
+                        t += (uint64_t)(xe - x0);
+                        ended = xe < L;   // the launch ends inside this row
+                        if (!ended) {
+                            const int y2 = (y + 2 < L) ? y + 2 : y + 2 - L;
+        #pragma unroll
+                            for (int i = 0; i < NW; ++i) {
+                                U[i] = C[i];
+                                C[i] = D[i];
+                            }
+                            rows.load(y2, D);
+                            y = (y + 1 == L) ? 0 : y + 1;
+                            blk += (uint64_t)(L / 4);
                         }
-                        rows.load(y2, D);
+                    }
+                    const uint64_t nwhole = ended ? 0u : (tend - t) / (uint64_t)L;
+                    if (nwhole > 0) {
+                        if (C1_ONLY || (t0p >> 34) == ((t0p + np - 1) >> 34)) {
+                            stream_rows_c1<L, RECORD, STRIDE>(rows, U, C, D, E, blk, y, nwhole, pkp);
+                        } else {
+        #pragma unroll 1
+                            for (uint64_t r = 0; r < nwhole; ++r) {
+                                const PhiloxSource src{blk + r * (uint64_t)(L / 4), &pkp};
+                                const int yr = (int)(((uint64_t)y + r) % (uint64_t)L);
+                                process_row<L, RECORD, false, PhiloxSource, STRIDE>(U, C, D, E, src);
+                                rows.store(yr, C);
+                                const int y2 = (yr + 2 < L) ? yr + 2 : yr + 2 - L;
+        #pragma unroll
+                                for (int i = 0; i < NW; ++i) {
+                                    U[i] = C[i];
+                                    C[i] = D[i];
+                                }
+                                rows.load(y2, D);
+                            }
+                        }
+                        t += nwhole * (uint64_t)L;
+                        y = (int)(((uint64_t)y + nwhole) % (uint64_t)L);
+                        blk += nwhole * (uint64_t)(L / 4);
+                    }
+                    if (!ended && t < tend) {   // the launch ends inside the next row
+                        const PhiloxSource src{blk, &pkp};
+                        process_row<L, RECORD, true, PhiloxSource, STRIDE>(U, C, D, E, src, 0, (int)(tend - t));
+                        rows.store(y, C);
                     }
                 }
-                t += nwhole * (uint64_t)L;
-                y = (int)(((uint64_t)y + nwhole) % (uint64_t)L);
-                blk += nwhole * (uint64_t)(L / 4);
             }
-            if (!ended && t < tend) {   // the launch ends inside the next row
-                const PhiloxSource src{blk, &pk};
-                process_row<L, RECORD, true, PhiloxSource, STRIDE>(U, C, D, E, src, 0, (int)(tend - t));
-                rows.store(y, C);
+            if (phase == 0) {
+                __syncthreads();
+                for (int i = tid; i < NB; i += nthr)
+                    sTab[(i + G) * STRIDE + kHistSlot] = 0u;
+                __syncthreads();
             }
         }
     }
@@ -979,7 +997,7 @@ template <int L, bool RECORD, bool GUARD = false, int STRIDE = kTableStride, boo
 __device__ __forceinline__ void batch_item(const SweepArgs &a, const BatchItem &it, unsigned char *smem)
 {
     constexpr uint64_t N = (uint64_t)L * (uint64_t)L;
-    if (!ANY_RANGE || (a.t0 % N == 0 && a.n % N == 0))
+    if (!ANY_RANGE || (a.t0 % N == 0 && a.n % N == 0 && a.n_therm % N == 0))
         sweep_block<L, RECORD, false, GUARD, STRIDE>(a, it.wbase, it.wpb, smem, a.layout);
     else
         sweep_block<L, RECORD, true, GUARD, STRIDE>(a, it.wbase, it.wpb, smem, a.layout);

@@ -53,7 +53,7 @@ template <int L>
 cudaError_t launch_full_l(const SweepArgs &a, int wpb, bool record, cudaStream_t s)
 {
     const uint64_t N = (uint64_t)L * (uint64_t)L;
-    if (a.t0 % N == 0 && a.n % N == 0)
+    if (a.t0 % N == 0 && a.n % N == 0 && a.n_therm % N == 0)
         return launch_full_p<L, false>(a, wpb, record, s);
     return launch_full_p<L, true>(a, wpb, record, s);
 }

@@ -375,12 +375,12 @@ cudaError_t launch_sweep(const SweepArgs &a, int wpb, bool record, cudaStream_t 
 
 cudaError_t launch_sweep_fused(const SweepArgs &a, int wpb, cudaStream_t s)
 {
-    const uint64_t N = (uint64_t)a.L * (uint64_t)a.L;
     const uint64_t total = a.n_therm + a.n;
-    // one launch: whole sweeps from a sweep boundary in the whole-sweep kernel, counter
-    // word 1 (t >> 34) the same for both phases
-    if (a.W > 0 && a.n_therm > 0 && a.n > 0 && has_full_kernel(a.L) && g_use_full_kernel && a.t0 % N == 0 &&
-        a.n_therm % N == 0 && a.n % N == 0 && total > a.n && (a.t0 >> 34) == ((a.t0 + total - 1) >> 34))
+    // one launch of the whole-sweep kernel (its whole-sweep form when both phases are
+    // whole sweeps from a sweep boundary, else its any-range form), counter word 1
+    // (t >> 34) the same for both phases
+    if (a.W > 0 && a.n_therm > 0 && a.n > 0 && has_full_kernel(a.L) && g_use_full_kernel && total > a.n &&
+        (a.t0 >> 34) == ((a.t0 + total - 1) >> 34))
         return launch_full(a, wpb, true, s);
     SweepArgs therm = a, rec = a;
     therm.n = a.n_therm;

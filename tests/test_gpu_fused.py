@@ -1,8 +1,8 @@
 """muca_thermalize_and_record (one weight iteration's sampling, Sec. 3: N_therm
 thermalization attempts, then N_updates recorded ones) against the oracle, bit for bit:
-the single launch that runs both phases (whole sweeps from a sweep boundary, typewriter
-order) and the two launches it falls back to (partial sweeps, random site order, a range
-across a step of Philox counter word 1)."""
+the single launch that runs both phases (typewriter order; whole sweeps from a sweep
+boundary or any attempt ranges) and the two launches it falls back to (random site
+order, no thermalization, a range across a step of Philox counter word 1)."""
 import numpy as np
 import pytest
 
@@ -59,11 +59,12 @@ def test_fused_whole_sweeps_equal_oracle(muca_mod, orc, layout, L, W, wpb):
     assert int(H.sum()) == W * 2 * N
 
 
-@pytest.mark.parametrize("L", [8, 32, 64])
-def test_fused_fallbacks_equal_oracle(muca_mod, orc, L):
-    """Attempt counts that are not whole sweeps (the Eq. (7) schedule's), a start inside
-    a sweep, a zero thermalization and random site order all take two launches; every
-    case equals the oracle."""
+@pytest.mark.parametrize("L", [8, 12, 32, 64])
+def test_fused_any_range_and_fallbacks_equal_oracle(muca_mod, orc, L):
+    """Attempt counts that are not whole sweeps (the Eq. (7) schedule's) and a start
+    inside a sweep run in one launch of the any-range form; a zero thermalization, random
+    site order and L = 12 (no whole-sweep kernel) take two launches.  Every case equals
+    the oracle."""
     W, seed = 70, 8
     N = L * L
     lnW = rand_weights(L, 3, 0.4 if L <= 8 else 0.05)
@@ -86,12 +87,14 @@ def test_fused_fallbacks_equal_oracle(muca_mod, orc, L):
 def test_fused_counter_word_boundary(muca_mod, orc, L):
     """Around t = 2^34, where Philox counter word 1 steps: a range that ends exactly at
     the step runs as one launch, one that crosses it as two (the second split again at
-    the step); both equal the oracle."""
+    the step), for whole sweeps and for partial ones; all equal the oracle."""
     W, seed = 40, 4
     N = L * L
     lnW = rand_weights(L, 6, 0.2)
     last = 2**34 // N * N                              # the last sweep boundary <= 2^34
-    for t0, nt, nr in [(last - 5 * N, 3 * N, 2 * N), (last - 3 * N, 2 * N, 3 * N), (last - N, 2 * N, N)]:
+    cases = [(last - 5 * N, 3 * N, 2 * N), (last - 3 * N, 2 * N, 3 * N), (last - N, 2 * N, N),
+             (2**34 - 2 * N - 5, N + 2, N + 3), (2**34 - N - 3, N, 7), (2**34 - 9, 4, 2 * N + 1)]
+    for t0, nt, nr in cases:
         with muca_mod.Muca(L, W, seed, walkers_per_block=32) as m:
             m.set_weights(lnW)
             m.set_attempt_counter(t0)
