@@ -24,6 +24,8 @@ struct NoAllocLaunch {
     int32_t prefix[kNoAllocMaxInstances + 1];   // work items before instance i
     int32_t n;
 };
+// kernel parameters may take 32 764 bytes (CUDA 12.1 and later)
+static_assert(sizeof(NoAllocLaunch) + sizeof(uint32_t *) <= 32764, "launch parameters too large");
 
 template <bool RECORD>
 __global__ void __launch_bounds__(256, 1) batch_noalloc_kernel(const __grid_constant__ NoAllocLaunch p,
