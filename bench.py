@@ -7,7 +7,7 @@ recursion; iteration budget 2e4 * L^2 recorded walker-sweeps (125 iterations).
 
 Reported:
   value        spin-flip attempts per second over K weight-iteration steps (one step =
-               table build + upload, thermalization, zeroed histogram, recorded sweeps,
+               weights upload + table build, thermalization, zeroed histogram, recorded sweeps,
                histogram read, flatness test and Eq. (4) recursion), device-timed with
                CUDA events, L2 flushed in each timed step before its sweep launch (the
                flush's window is not counted);
@@ -410,13 +410,14 @@ def run_native(args):
     flat = [False]
 
     def step(ev=None):
-        """One weight iteration through the C ABI (table build and upload; zeroed
-        histogram, thermalization and recorded sweeps in one muca_thermalize_and_record
-        call, one kernel launch; histogram read; the min/mean flatness test and the
-        Eq. (4) recursion, muca_flatness and muca_update_weights).  ev = five CUDA events
+        """One weight iteration through the C ABI (weights upload, the table built on the
+        device; zeroed histogram, thermalization and recorded sweeps in one
+        muca_thermalize_and_record call, one kernel launch; histogram read; the min/mean
+        flatness test and the Eq. (4) recursion, muca_flatness and muca_update_weights).
+        ev = five CUDA events
         on the instance's stream: step start, the L2 flush's start and end, after the
         sampling call, after the host recursion.  In a timed step the L2 flush (a 256 MiB
-        write) runs between the table upload and the sampling call: the GPU is busy with
+        write) runs between the weights upload and the sampling call: the GPU is busy with
         it while the host enqueues the launch, so that the sampling window holds GPU work
         only; the flush's own window is left out of the step's time."""
         if ev:
@@ -525,7 +526,7 @@ def run_native(args):
         "table_ms_per_step": sum(table_ms) / len(table_ms),
         "sweep_launch_ms_per_step": sum(sample_ms) / len(sample_ms),
         "e2e": {"value": e2e_value, "unit": "attempts/s",
-                "h2d_bytes_per_step": (N + 1) * 5 * 4, "d2h_bytes_per_step": (N + 1) * 8 + 4},
+                "h2d_bytes_per_step": (N + 1) * 8, "d2h_bytes_per_step": (N + 1) * 8 + 4},
         "gpu_launches": args.steps,
         "roofline": {"bound": "alu", "achieved": achieved_tops, "peak": peak_tops, "unit": "Tops/s (int32)",
                      "frac": achieved_tops / peak_tops, "traffic": traffic,

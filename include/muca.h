@@ -237,8 +237,9 @@ int muca_set_allocator(void *(*alloc)(size_t size, void *ctx), void (*release)(v
                        void *ctx);
 
 /* Copies ln W(e), e = 0 .. N (FP64, n_bins = N + 1), into the instance and rebuilds the
- * acceptance-threshold table (Sec. 2.3).  Errors: MUCA_EINVAL (wrong n_bins, NULL,
- * non-finite value). */
+ * acceptance-threshold table (Sec. 2.3) on the device, on the instance's stream (the
+ * thresholds equal muca_build_table's bit for bit).  Errors: MUCA_EINVAL (wrong n_bins,
+ * NULL, non-finite value). */
 int muca_set_weights(muca_t h, const double *lnW, size_t n_bins);
 
 /* Histogram reduction for a simulation spread over several instances (Sec. 2.2: the

@@ -69,13 +69,17 @@ void build_table(int32_t L, const std::vector<double> &lnW, uint32_t *T)
         }
 }
 
+// ln W to the device (staged through the pinned table buffer, which holds 20 bytes per
+// energy), then the thresholds built there by the same arithmetic as build_table.
 int upload_table(muca_t h)
 {
     MUCA_CUDA(cudaEventSynchronize(h->table_copied), "waiting for the previous table upload");
-    build_table(h->L, h->lnW, h->h_table);
-    const size_t bytes = (size_t)(h->N + 1) * 5 * sizeof(uint32_t);
-    MUCA_CUDA(cudaMemcpyAsync(h->d_table, h->h_table, bytes, cudaMemcpyHostToDevice, h->stream), "table upload");
-    MUCA_CUDA(cudaEventRecord(h->table_copied, h->stream), "table upload event");
+    double *stage = reinterpret_cast<double *>(h->h_table);
+    std::copy(h->lnW.begin(), h->lnW.end(), stage);
+    MUCA_CUDA(cudaMemcpyAsync(h->d_lnW, stage, h->lnW.size() * sizeof(double), cudaMemcpyHostToDevice, h->stream),
+              "weights upload");
+    MUCA_CUDA(cudaEventRecord(h->table_copied, h->stream), "weights upload event");
+    MUCA_CUDA(muca::launch_table(h->N, h->d_lnW, h->d_table, h->stream), "table build");
     return MUCA_OK;
 }
 
@@ -435,7 +439,8 @@ int muca_create_ex(const muca_options *opt, muca_t *out)
     const size_t off_T = off_e + align256((size_t)h->W * sizeof(int32_t));
     const size_t off_H = off_T + align256(nb * 5 * sizeof(uint32_t));
     const size_t off_err = off_H + align256(nb * sizeof(unsigned long long));
-    const size_t total = off_err + 256;
+    const size_t off_W = off_err + 256;
+    const size_t total = off_W + align256(nb * sizeof(double));
 
     auto cleanup = [&](int rc) {
         muca_destroy(h);
@@ -457,6 +462,7 @@ int muca_create_ex(const muca_options *opt, muca_t *out)
     h->d_table = reinterpret_cast<uint32_t *>(base + off_T);
     h->d_hist = reinterpret_cast<unsigned long long *>(base + off_H);
     h->d_err = reinterpret_cast<uint32_t *>(base + off_err);
+    h->d_lnW = reinterpret_cast<double *>(base + off_W);
     err = cudaMallocHost(reinterpret_cast<void **>(&h->h_table), nb * 5 * sizeof(uint32_t));
     if (err != cudaSuccess)
         return cleanup(cuda_fail(err, "pinned table buffer"));

@@ -339,7 +339,7 @@ size_t instance_device_bytes(int32_t L, int32_t layout, int64_t W)
     const size_t nb = (size_t)L * L + 1;
     return align256(muca::lattice_bytes(L, layout == MUCA_LAYOUT_PACKED ? MUCA_LAYOUT_PACKED : MUCA_LAYOUT_INT8, W)) +
            align256((size_t)W * sizeof(int32_t)) + align256(nb * 5 * sizeof(uint32_t)) +
-           align256(nb * sizeof(unsigned long long)) + 256;
+           align256(nb * sizeof(unsigned long long)) + 256 + align256(nb * sizeof(double));
 }
 
 }  // namespace

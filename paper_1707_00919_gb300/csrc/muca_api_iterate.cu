@@ -302,12 +302,10 @@ int muca_iterate_device(muca_t h, const muca_params *p_in, int32_t iterations_pe
     const int32_t N = h->N;
     const size_t nb = (size_t)N + 1;
     if (!h->iter_block) {
-        const size_t off_state = align256(nb * sizeof(double));
-        h->iter_block = device_alloc(h->alloc, off_state + align256(sizeof(muca::IterState)));
+        h->iter_block = device_alloc(h->alloc, align256(sizeof(muca::IterState)));
         if (!h->iter_block)
             return fail(MUCA_ENOMEM, "device allocation for the iteration state failed");
-        h->d_lnW = static_cast<double *>(h->iter_block);
-        h->d_iter = reinterpret_cast<muca::IterState *>(static_cast<char *>(h->iter_block) + off_state);
+        h->d_iter = static_cast<muca::IterState *>(h->iter_block);
         MUCA_CUDA(cudaMallocHost(reinterpret_cast<void **>(&h->h_iter), sizeof(muca::IterState)),
                   "pinned iteration state");
         MUCA_CUDA(muca::configure_iter_metric(N), "metric kernel shared memory");
@@ -321,9 +319,7 @@ int muca_iterate_device(muca_t h, const muca_params *p_in, int32_t iterations_pe
     h->h_iter->prev_hi = p.resume ? h->sched.prev_hi : -1;
     MUCA_CUDA(cudaMemcpyAsync(h->d_iter, h->h_iter, sizeof(muca::IterState), cudaMemcpyHostToDevice, h->stream),
               "iteration state upload");
-    MUCA_CUDA(cudaMemcpyAsync(h->d_lnW, h->lnW.data(), nb * sizeof(double), cudaMemcpyHostToDevice, h->stream),
-              "weights upload");
-    rc = upload_table(h);
+    rc = upload_table(h);   // the weights to the device and the first table
     if (rc)
         return rc;
     const uint32_t *done = &h->d_iter->done;

@@ -75,8 +75,8 @@ struct muca_s {
     uint32_t *h_err = nullptr;
     cudaEvent_t table_copied = nullptr;    // last table upload has left h_table
     std::vector<double> lnW;
-    void *iter_block = nullptr;      // device ln W and iteration state (muca_iterate_device)
-    double *d_lnW = nullptr;
+    void *iter_block = nullptr;      // device iteration state (muca_iterate_device)
+    double *d_lnW = nullptr;         // device ln W (in block): the table is built from it
     muca::IterState *d_iter = nullptr;
     muca::IterState *h_iter = nullptr;   // pinned staging of the state
     uint64_t t = 0;                  // attempt counter (tag 0 stream)

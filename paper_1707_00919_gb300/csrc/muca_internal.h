@@ -69,6 +69,10 @@ cudaError_t launch_iter_recursion(const IterState *st, int32_t N, double *lnW, c
                                   cudaStream_t s);
 cudaError_t launch_iter_table(const IterState *st, int32_t N, const double *lnW, uint32_t *table, cudaStream_t s);
 
+// Thresholds T[e][k] of the weights lnW[N + 1] on the device (the host's build_table
+// arithmetic, bit for bit): every weight upload of an instance.
+cudaError_t launch_table(int32_t N, const double *lnW, uint32_t *table, cudaStream_t s);
+
 // One work item of the batched kernel: walkers wbase .. wbase + wpb - 1 of instance inst.
 struct BatchItem {
     int32_t inst;

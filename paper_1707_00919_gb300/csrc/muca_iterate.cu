@@ -181,16 +181,30 @@ __global__ void iter_recursion_kernel(const IterState *st, int32_t N, double *ln
         lnW[e] = __dsub_rn(lnW[e], fp64::log((double)H[e]));
 }
 
-// Thresholds T[e][k] of the next iteration (the rule of muca.h).
+// Threshold T[e][k], i = 5 e + k (the rule of muca.h, the arithmetic of the host's
+// build_table).
+__device__ __forceinline__ uint32_t table_entry(int32_t N, const double *lnW, int32_t i)
+{
+    const int32_t e = i / 5, k = i - 5 * e, to = e + 2 - k;
+    return (to >= 0 && to <= N) ? fp64::threshold(__dsub_rn(lnW[to], lnW[e])) : 0u;
+}
+
+// Thresholds of the next iteration, when the metric kernel asked for them.
 __global__ void iter_table_kernel(const IterState *st, int32_t N, const double *lnW, uint32_t *T)
 {
     if (!st->update)
         return;
     const int32_t i = blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= (N + 1) * 5)
-        return;
-    const int32_t e = i / 5, k = i - 5 * e, to = e + 2 - k;
-    T[i] = (to >= 0 && to <= N) ? fp64::threshold(__dsub_rn(lnW[to], lnW[e])) : 0u;
+    if (i < (N + 1) * 5)
+        T[i] = table_entry(N, lnW, i);
+}
+
+// Thresholds of the given weights (every weight upload of an instance).
+__global__ void table_kernel(int32_t N, const double *lnW, uint32_t *T)
+{
+    const int32_t i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < (N + 1) * 5)
+        T[i] = table_entry(N, lnW, i);
 }
 
 }  // namespace
@@ -221,6 +235,13 @@ cudaError_t launch_iter_recursion(const IterState *st, int32_t N, double *lnW, c
                                   cudaStream_t s)
 {
     iter_recursion_kernel<<<(N + 1 + 127) / 128, 128, 0, s>>>(st, N, lnW, hist);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_table(int32_t N, const double *lnW, uint32_t *table, cudaStream_t s)
+{
+    const int32_t n = (N + 1) * 5;
+    table_kernel<<<(n + 127) / 128, 128, 0, s>>>(N, lnW, table);
     return cudaGetLastError();
 }
 

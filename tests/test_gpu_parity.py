@@ -66,6 +66,21 @@ def test_table_matches_oracle(muca_mod, orc):
     assert np.array_equal(T, orc.build_table(L, lnW))
 
 
+@pytest.mark.parametrize("L", [4, 8, 24, 64])
+def test_device_table_equals_host_and_oracle(muca_mod, orc, L):
+    """muca_set_weights builds the thresholds on the device; they equal the host's
+    muca_build_table and the oracle's bit for bit, including thresholds that round to
+    the accept-all word and ones that underflow to 0."""
+    lnW = rand_weights(L, 11 * L, 4.0)
+    lnW[3] = lnW[5] - 1e-18
+    lnW[L] = lnW[L + 2] + 80.0
+    with muca_mod.Muca(L, 40, 2) as m:
+        m.set_weights(lnW)
+        T = m.get_table()
+    assert np.array_equal(T, muca_mod.muca_build_table(L, lnW))
+    assert np.array_equal(T, orc.build_table(L, lnW))
+
+
 def run_both(muca_mod, orc, L, W, seed, layout, wpb, lnW, plan):
     """plan: list of (n_attempts, record, reset_before).  Returns device and oracle
     (lattice, energies, histogram)."""
