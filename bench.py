@@ -432,7 +432,7 @@ def run_native(args):
         if ev:
             ev[3].record(stream)
         H = m.get_histogram()
-        flat[0] = M.muca_flatness(L_SIDE, H)["min_over_mean"] >= 0.8
+        flat[0] = M.muca_flatness(L_SIDE, H, measures=("min_over_mean",))["min_over_mean"] >= 0.8
         M.muca_update_weights(L_SIDE, lnW, H)
         if ev:
             ev[4].record(stream)

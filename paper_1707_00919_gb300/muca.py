@@ -259,15 +259,21 @@ def muca_update_weights(L: int, lnW: np.ndarray, H) -> None:
     _check(C.load().muca_update_weights(L, _p(lnW, ctypes.c_double), _p(h, ctypes.c_uint64), lnW.size))
 
 
-def muca_flatness(L: int, H, prev_range: tuple[int, int] = (-1, -1)) -> dict:
+def muca_flatness(L: int, H, prev_range: tuple[int, int] = (-1, -1),
+                  measures: tuple[str, ...] = ("min_over_mean", "kl", "chebyshev")) -> dict:
     """min/mean, d_k (Eq. 6, reference width from prev_range and H's range) and d_c
-    (Eq. A.1) of a histogram, and its visited range."""
+    (Eq. A.1) of a histogram, and its visited range; only the named measures are
+    computed (the others are passed as NULL)."""
     h = np.ascontiguousarray(H, dtype=np.uint64)
-    mm, kl, dc = ctypes.c_double(), ctypes.c_double(), ctypes.c_double()
+    out = {name: ctypes.c_double() for name in ("min_over_mean", "kl", "chebyshev") if name in measures}
+    ref = {name: ctypes.byref(v) for name, v in out.items()}
     lo, hi = ctypes.c_int32(), ctypes.c_int32()
-    _check(C.load().muca_flatness(L, _p(h, ctypes.c_uint64), h.size, prev_range[0], prev_range[1], ctypes.byref(mm),
-                                  ctypes.byref(kl), ctypes.byref(dc), ctypes.byref(lo), ctypes.byref(hi)))
-    return {"min_over_mean": mm.value, "kl": kl.value, "chebyshev": dc.value, "range": (lo.value, hi.value)}
+    _check(C.load().muca_flatness(L, _p(h, ctypes.c_uint64), h.size, prev_range[0], prev_range[1],
+                                  ref.get("min_over_mean"), ref.get("kl"), ref.get("chebyshev"), ctypes.byref(lo),
+                                  ctypes.byref(hi)))
+    res = {name: v.value for name, v in out.items()}
+    res["range"] = (lo.value, hi.value)
+    return res
 
 
 class IterationLog:
