@@ -51,7 +51,7 @@ OPS_PER_ATTEMPT = 35.0
 # Warp instructions the step's whole-sweep launch issues per attempt and warp (ncu
 # count, profiles/sweep_full_kernel_L32_W16384_int8.md): converts an instruction issue
 # rate into this roofline's algorithmic operations.
-INSTR_PER_ATTEMPT = 33.05
+INSTR_PER_ATTEMPT = 31.13
 WORKLOAD = (f"muca2d_ising_L{L_SIDE}_W{WALKERS}_int8_therm{THERM_SWEEPS}_rec{SWEEPS_PER_ITER}")
 
 
@@ -527,7 +527,7 @@ def run_native(args):
         "sweep_launch_ms_per_step": sum(sample_ms) / len(sample_ms),
         "e2e": {"value": e2e_value, "unit": "attempts/s",
                 "h2d_bytes_per_step": (N + 1) * 8, "d2h_bytes_per_step": (N + 1) * 8 + 4},
-        "gpu_launches": args.steps,
+        "gpu_launches": 2 * args.steps,   # per step: table_kernel, sweep_full_kernel
         "roofline": {"bound": "alu", "achieved": achieved_tops, "peak": peak_tops, "unit": "Tops/s (int32)",
                      "frac": achieved_tops / peak_tops, "traffic": traffic,
                      "kernel": "sweep_full_kernel<32,int8,record> (31 thermalization + 10 recorded "

@@ -52,7 +52,9 @@ __device__ __forceinline__ uint32_t bit_at(RowT w, int x)
 // memory latency off the attempt-to-attempt dependency chain.  Both candidates are
 // compared with the random word as soon as they arrive, so the decision itself is one
 // select of two booleans, and both load addresses of the next-but-one attempt are
-// formed before the decision and selected by it.
+// formed before the decision and selected by it.  So is, in the whole-row stream, the
+// row address the next attempt moves to if it flips (E + its step for both outcomes of
+// the current attempt): one select after a decision instead of a select and an add.
 // ---------------------------------------------------------------------------------
 template <int L>
 struct RowOf {
@@ -535,7 +537,8 @@ struct AttemptStream {
     uint32_t E;                      // table row address of the current energy
     bool prev_acc;                   // the previous attempt flipped
     uint32_t T0n, T1n, T0nn, T1nn;   // candidates of the next two attempts
-    uint32_t d0_cur, d1_cur, d0_next, d1_next;
+    uint32_t Eacc;                   // row address if the current attempt flips
+    uint32_t d0_next, d1_next;
 
     // Counts of the row (U above, C, D below) in nibble fields: K0 if the left
     // neighbour did not flip, K1 if it did.
@@ -564,12 +567,13 @@ struct AttemptStream {
         const uint32_t J0a = field_x4(K0[0], 0), J0b = field_x4(K0[0], 1), J1b = field_x4(K1[0], 1);
         E = E0;
         prev_acc = false;
-        d0_cur = d1_cur = kD2 - kDJ * J0a;
+        const uint32_t d0 = kD2 - kDJ * J0a;
+        Eacc = E0 + d0;
         d0_next = kD2 - kDJ * J0b;
         d1_next = kD2 - kDJ * J1b;
         T0n = T1n = lds_u32(E + J0a);
         T0nn = lds_u32(E + J0b);
-        T1nn = lds_u32(E + d0_cur + J1b);
+        T1nn = lds_u32(E + d0 + J1b);
     }
 
     // One row (U above, C updated in place, D below, D2 the row below D); on return the
@@ -603,8 +607,6 @@ struct AttemptStream {
 #pragma unroll
             for (int u = 0; u < 4; ++u) {
                 const int x = xb + u;
-                const uint32_t dsel = prev_acc ? d1_cur : d0_cur;
-                const uint32_t Eacc = Eres + dsel;
                 const bool c0 = words[u] < T0n, c1 = words[u] < T1n;
                 const bool acc = prev_acc ? c1 : c0;
                 const uint32_t Epost = acc ? Eacc : Eres;
@@ -633,12 +635,14 @@ struct AttemptStream {
                 }
                 T0n = T0nn;
                 T1n = T1nn;
+                // the next attempt's flipped row, formed from both outcomes before this
+                // decision and selected by it
+                const uint32_t t1 = Eacc + d1_next, t0 = Eres + d0_next;
                 const uint32_t a0 = acc ? Eacc + J0c : Eres + J0c;
-                const uint32_t a1 = acc ? Eacc + d1_next + J1c : Eres + d0_next + J1c;
+                const uint32_t a1 = acc ? t1 + J1c : t0 + J1c;
                 T0nn = lds_u32(a0);
                 T1nn = lds_u32(a1);
-                d0_cur = d0_next;
-                d1_cur = d1_next;
+                Eacc = acc ? t1 : t0;
                 d0_next = kD2 - kDJ * J0c;
                 d1_next = kD2 - kDJ * J1c;
                 Eres = Epost;
