@@ -15,7 +15,7 @@ struct muca_batch_s {
     Allocator alloc;
     cudaStream_t stream = nullptr;
     void *block = nullptr;
-    muca::SweepArgs *d_args = nullptr;    // [2 n]: thermalization launch, recording launch
+    muca::SweepArgs *d_args = nullptr;    // [2 n]: thermalization, recording (with n_therm: both)
     muca::BatchItem *d_items = nullptr;   // capacity: all items of all instances
     uint32_t *d_counter = nullptr;        // two work counters
     muca::SweepArgs *h_args = nullptr;    // pinned staging of d_args
@@ -208,10 +208,10 @@ int read_back(muca_batch_t b, const std::vector<int32_t> &active)
 
 // One weight iteration of the members `active` (indices into b->inst): member j
 // thermalizes therm[j] attempts per walker and records rec[j], all members in one
-// replay of the iteration graph, or, when some member records more attempts than one
-// launch's 32-bit shared counts take, as a thermalization launch and several recording
-// launches issued directly.  Afterwards each member's histogram is in its pinned buffer
-// and its attempt counter is advanced.
+// replay of the iteration graph (one launch for both phases), or, when some member
+// records more attempts than one launch's 32-bit shared counts take, as a thermalization
+// launch and several recording launches issued directly.  Afterwards each member's
+// histogram is in its pinned buffer and its attempt counter is advanced.
 int batch_run_iteration(muca_batch_t b, const std::vector<int32_t> &active, const std::vector<uint64_t> &therm,
                         const std::vector<uint64_t> &rec)
 {

@@ -100,6 +100,21 @@ def test_flatness_measures_match_oracle(mm, orc, L):
             assert got["kl"] == orc.kullback_leibler(L, H, float(q))
 
 
+def test_flatness_selected_measures(mm):
+    """Only the named measures are computed (the others are passed as NULL); each equals
+    the value of the call that computes all three, and the range is always returned."""
+    L = 16
+    N = L * L
+    H = np.random.default_rng(5).integers(1, 500, N + 1).astype(np.uint64)
+    full = mm.muca_flatness(L, H, (2, N - 3))
+    for measures in [("min_over_mean",), ("kl",), ("chebyshev",), ("min_over_mean", "kl")]:
+        got = mm.muca_flatness(L, H, (2, N - 3), measures=measures)
+        assert set(got) == set(measures) | {"range"}
+        assert got["range"] == full["range"]
+        for k in measures:
+            assert got[k] == full[k]
+
+
 def test_flatness_rejects_bad_input(mm):
     N = 64
     with pytest.raises(mm.MucaError):
