@@ -216,9 +216,10 @@ bool get(FILE *f, T *v, size_t n)
 // the larger block.
 int default_walkers_per_block(int32_t L, int32_t layout, int64_t W)
 {
-    int dev = 0, sms = 1;
-    cudaGetDevice(&dev);
-    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    int dev = 0, sms = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) !=
+                                                   cudaSuccess || sms < 1)
+        sms = 1;   // no device answer: size as for one SM (the launch itself reports the error)
     const size_t limit = muca::sweep_smem_limit();
     int best = 64;
     int64_t best_cost = INT64_MAX;

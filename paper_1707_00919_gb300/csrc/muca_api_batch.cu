@@ -425,9 +425,12 @@ int muca_batch_create(const muca_t *instances, int32_t n, muca_batch_t *out)
         err = muca::configure_batch(b->smem);
     if (err != cudaSuccess)
         return cleanup(cuda_fail(err, "batch set-up"));
-    int dev = 0, sms = 1;
-    cudaGetDevice(&dev);
-    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    int dev = 0, sms = 0;
+    err = cudaGetDevice(&dev);
+    if (err == cudaSuccess)
+        err = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    if (err != cudaSuccess)
+        return cleanup(cuda_fail(err, "multiprocessor count"));
     const int occ = muca::batch_resident_blocks(b->smem);
     if (occ < 1)
         return cleanup(fail(MUCA_EINVAL, "batched kernel does not fit an SM with %zu bytes of shared memory", b->smem));

@@ -339,8 +339,9 @@ size_t sweep_smem_bytes(int L, int wpb, bool record)
 size_t sweep_smem_limit()
 {
     int dev = 0, v = 0;
-    cudaGetDevice(&dev);
-    cudaDeviceGetAttribute(&v, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+    if (cudaGetDevice(&dev) != cudaSuccess ||
+        cudaDeviceGetAttribute(&v, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev) != cudaSuccess)
+        return 0;   // nothing fits: callers report it
     return (size_t)v;
 }
 
@@ -472,9 +473,10 @@ int resident_blocks(int L, int layout, int wpb)
     }
     // the generic kernel: bounded by shared memory and threads
     int dev = 0, smem_sm = 0, thr_sm = 0;
-    cudaGetDevice(&dev);
-    cudaDeviceGetAttribute(&smem_sm, cudaDevAttrMaxSharedMemoryPerMultiprocessor, dev);
-    cudaDeviceGetAttribute(&thr_sm, cudaDevAttrMaxThreadsPerMultiProcessor, dev);
+    if (cudaGetDevice(&dev) != cudaSuccess ||
+        cudaDeviceGetAttribute(&smem_sm, cudaDevAttrMaxSharedMemoryPerMultiprocessor, dev) != cudaSuccess ||
+        cudaDeviceGetAttribute(&thr_sm, cudaDevAttrMaxThreadsPerMultiProcessor, dev) != cudaSuccess)
+        return 0;   // no resident block: callers skip this block size
     const size_t need = sweep_smem_bytes(L, wpb, true) + 1024;
     return (int)std::min((size_t)smem_sm / need, (size_t)(thr_sm / wpb));
 }
