@@ -236,6 +236,8 @@ int batch_run_iteration(muca_batch_t b, const std::vector<int32_t> &active, cons
         chunked = chunked || rec[j] > cap;
     for (size_t j = 0; j < nm; ++j) {
         muca_t h = b->inst[(size_t)active[j]];
+        // the member's own last upload (muca_set_weights) may still read its staging buffer
+        MUCA_CUDA(cudaEventSynchronize(h->table_copied), "waiting for the member's weights upload");
         build_table(h->L, h->lnW, h->h_table);
         b->h_args[j] = make_args(h, h->t, therm[j]);
         if (chunked) {   // a thermalization launch, then recording launches of at most cap attempts
